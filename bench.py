@@ -1,0 +1,399 @@
+"""Throughput of the fast BTTB operator: G m and G^T d applies per second.
+
+One step = one forward product d = G m plus one transpose product m' = G^T d
+(Algorithm multbttb, t = 1 and t = 2) on the 300 x 250-station, 60-layer
+gravity grid with 10 % padding per side (the largest workload that fits one
+GPU many times over), FP32 apply, FP64 set-up excluded from the timing as the
+paper excludes FFTW planning (Sec. 5, Remark).  Prints one JSON line.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+N > 1 (launched by torch.distributed.run): every rank runs an independent
+replica on its own GPU (the operator has no exchange step on one GPU's data);
+value = applies of all ranks / the slowest rank's time ("replicas only").
+
+--impl reference times the CPU oracle (dense long-double prism entries, direct
+summation) on bounded samples of the same workload on the host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "grav300"
+METRIC = "G·m and G^T·d applies/s (FP32 vs FP64 on GPU) at rel err ≤1e-5; % HBM roofline"
+UNIT = "applies/s"
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["paper_1912_06976_gb300/csrc/apply.cu", "paper_1912_06976_gb300/csrc/gm_kernels.cuh",
+                  "paper_1912_06976_gb300/csrc/gm_common.cuh"]
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------- ranks
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def reduce_max_sum(t_ms: float, units: float):
+    """(max over ranks of t_ms, sum over ranks of units); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return t_ms, units
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    a = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+    b = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(a.item()), float(b.item())
+
+
+def barrier():
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """dram bytes per launch from the committed ncu summary, if it was taken on the current source."""
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    for ln in open(path):
+        if ln.startswith("#") or not ln.strip():
+            continue
+        f = dict(kv.split("=", 1) for kv in ln.split() if "=" in kv)
+        if f.get("kernel") == kernel and f.get("source_sha") == want:
+            try:
+                return float(f["dram_bytes_per_launch"])
+            except (KeyError, ValueError):
+                return None
+    return None
+
+
+def cpu_oracle_sample(w, budget_s: float = 12.0, min_batches: int = 1):
+    """Times the oracle's transpose product on whole batches of cells (one cell per thread
+    per batch) until the budget is spent; each cell is one column of G (m entries)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1912_06976_gb300 import workloads as W
+
+    geom = O.Geometry(w.sx, w.sy, w.nz, w.dx, w.dy, w.zplanes, w.pxl, w.pxr, w.pyl, w.pyr, w.kind,
+                      w.incl_deg, w.decl_deg, w.F_nT)
+    d = W.data(w.name, 0)
+    threads = O.threads()
+    rng = np.random.default_rng(1234)
+    cells, t_total, batches = 0, 0.0, 0
+    while batches < min_batches or t_total < budget_s:
+        idx = rng.choice(w.n, size=threads, replace=False)
+        t0 = time.perf_counter()
+        O.transpose(geom, d, idx)
+        t_total += time.perf_counter() - t0
+        cells += threads
+        batches += 1
+        if t_total > 3 * budget_s:
+            break
+    entries = cells * w.m
+    sec_per_entry = t_total / entries
+    apply_s = sec_per_entry * w.m * w.n  # a forward or transpose product evaluates all m*n entries
+    return {"value": 1.0 / apply_s, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"G^T d at {cells} sampled cells ({entries} entries of G, {t_total:.1f} s), scaled to "
+                      f"the m*n = {w.m * w.n} entries one forward or transpose product evaluates",
+            "seconds": t_total}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1912_06976_gb300 import workloads as W
+
+    w = W.WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, budget_s=0.0, min_batches=1)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        r = cpu_oracle_sample(w, budget_s=0.0, min_batches=1)
+        vals.append(r["value"])
+        secs += r["seconds"]
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f80/f128 (long double)",
+            "data": "synthetic", "config": workload_config(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": f"each step: G^T d at {r['cores']} sampled cells (one per thread), "
+                                       f"scaled to m*n entries per product"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(w, info=None):
+    cfg = {"workload": f"{w.name}: {'gravity' if w.kind == 0 else 'magnetic'} {w.sx}x{w.sy} stations, "
+                       f"{w.nz} layers of {w.dx:g} m cells, padding {w.pxl}/{w.pyl} cells per side",
+           "stations": w.m, "cells": w.n, "step": "1 forward + 1 transpose product (2 applies)",
+           "apply_precision": "fp32 (fp64 set-up)", "l2": "flushed between steps (256 MiB write, untimed)"}
+    if info is not None:
+        cfg["fft"] = f"{info.fft_nx}x{info.fft_ny}"
+    return cfg
+
+
+# ----------------------------------------------------------------------------- our arm
+def time_steps(op, m, d, outd, outm, flush, steps):
+    """Per-step CUDA-event times (ms) of forward + transpose, L2 flushed between steps."""
+    import torch
+
+    st = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(st)
+        op.forward(m, out=outd)
+        op.transpose(d, out=outm)
+        ends[k].record(st)
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1912_06976_gb300 import gravmag as gm
+    from paper_1912_06976_gb300 import workloads as W
+
+    w = W.WORKLOADS[args.workload]
+    op = gm.Operator.from_workload(w, precision=gm.F32)
+    inf = op.info
+    m = torch.as_tensor(W.model(w.name, 0), dtype=torch.float32, device="cuda").contiguous()
+    d = torch.as_tensor(W.data(w.name, 0), dtype=torch.float32, device="cuda").contiguous()
+    outd = torch.empty(op.data_shape, dtype=torch.float32, device="cuda")
+    outm = torch.empty(op.model_shape, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    time_steps(op, m, d, outd, outm, flush, max(args.warmup, 3))
+    op.enable_timing(6 * args.steps + 16)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    per_step = time_steps(op, m, d, outd, outm, flush, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ktimes = op.kernel_times()
+    op.enable_timing(0)
+    t_ms = sum(per_step)
+    t_max, applies = reduce_max_sum(t_ms, 2.0 * args.steps)
+    value = applies / (t_max / 1000.0)
+    gpu_launches = sum(v[0] for v in ktimes.values())
+
+    # roofline of the dominant kernel: algorithmic bytes per launch / its mean launch time
+    w_el = 4
+    spec_bytes = 2 * w_el * inf.nz * inf.fft_ny * inf.spec_nx
+    alg = {"fwd_rows_r2c": w_el * inf.n_model, "fwd_cols_mac": spec_bytes, "fwd_rows_c2r": w_el * inf.n_data,
+           "tr_rows_r2c": w_el * inf.n_data, "tr_cols": spec_bytes, "tr_rows_c2r": w_el * inf.n_model}
+    dom = max(ktimes, key=lambda k: ktimes[k][1])
+    dom_ms = ktimes[dom][1] / ktimes[dom][0]
+    peak, peak_kind = measured_peaks()
+    achieved = alg[dom] / (dom_ms / 1e3) / 1e9
+    traffic = profiled_traffic(dom, w.name)
+    apply_bytes = w_el * (inf.n_model + inf.n_data) + spec_bytes  # per forward or transpose product
+    step_ms = t_ms / args.steps
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                "traffic": traffic, "algorithmic_bytes_per_launch": alg[dom],
+                "kernel_ms_per_launch": dom_ms,
+                "apply_effective_gbs": 2 * apply_bytes / (step_ms / 1e3) / 1e9,
+                "apply_frac": 2 * apply_bytes / (step_ms / 1e3) / 1e9 / peak,
+                "kernel_share": {k: v[1] / sum(x[1] for x in ktimes.values()) for k, v in ktimes.items()}}
+
+    # end to end through the host-buffer entry points (pinned host memory, copies timed)
+    mh = m.cpu().pin_memory()
+    dh = d.cpu().pin_memory()
+    od = torch.empty(op.data_shape, dtype=torch.float32).pin_memory()
+    om = torch.empty(op.model_shape, dtype=torch.float32).pin_memory()
+    for _ in range(3):
+        op.forward_host(mh, od)
+        op.transpose_host(dh, om)
+    k_e2e = max(5, min(args.steps, 50))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        op.forward_host(mh, od)
+        op.transpose_host(dh, om)
+    t_e2e = (time.perf_counter() - t0) * 1e3
+    te_max, e_app = reduce_max_sum(t_e2e, 2.0 * k_e2e)
+    e2e = {"value": e_app / (te_max / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": 4 * (inf.n_model + inf.n_data), "d2h_bytes_per_step": 4 * (inf.n_data + inf.n_model),
+           "api": "apply_forward_host + apply_transpose_host (pinned host buffers)", "steps": k_e2e}
+
+    # precision: FP32 against the FP64 GPU run (whole vectors) and against the oracle samples
+    extra = {}
+    if not args.no_fp64:
+        op64 = gm.Operator.from_workload(w, precision=gm.F64)
+        m64, d64 = m.double(), d.double()
+        od64 = torch.empty(op.data_shape, dtype=torch.float64, device="cuda")
+        om64 = torch.empty(op.model_shape, dtype=torch.float64, device="cuda")
+        time_steps(op64, m64, d64, od64, om64, flush, 2)
+        k64 = max(3, min(args.steps, 10))
+        t64 = sum(time_steps(op64, m64, d64, od64, om64, flush, k64))
+        extra["fp64"] = {"value": 2 * k64 / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / k64,
+                         "setup_ms": op64.info.setup_ms}
+        op.forward(m, out=outd)
+        op.transpose(d, out=outm)
+        torch.cuda.synchronize()
+        extra["rel_err_fp32_vs_fp64"] = {
+            "forward": gm.rel_err(outd.double().cpu().numpy(), od64.cpu().numpy()),
+            "transpose": gm.rel_err(outm.double().cpu().numpy(), om64.cpu().numpy())}
+        gpath = os.path.join(ROOT, "tests", "golden", f"sampled_{w.name}.json")
+        if os.path.exists(gpath):
+            g = json.load(open(gpath))
+            extra["rel_err_vs_oracle_samples"] = {
+                "fp32_forward": gm.rel_err(outd.double().cpu().numpy().ravel()[g["forward_stations"]], g["forward"]),
+                "fp32_transpose": gm.rel_err(outm.double().cpu().numpy().ravel()[g["transpose_cells"]],
+                                             g["transpose"]),
+                "fp64_forward": gm.rel_err(od64.cpu().numpy().ravel()[g["forward_stations"]], g["forward"]),
+                "fp64_transpose": gm.rel_err(om64.cpu().numpy().ravel()[g["transpose_cells"]], g["transpose"])}
+        op64.close()
+    extra["setup_ms"] = inf.setup_ms
+    extra["kernel_ms_per_step"] = {k: v[1] / args.steps for k, v in ktimes.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(w)
+        cpu.pop("seconds", None)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {**workload_config(w, inf), "parallelism": f"replicas{world}" if world > 1 else "1 GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+                "clocks": clk, **extra}
+        print(json.dumps(line))
+    op.close()
+    if world > 1:
+        dist.destroy_process_group()
+    del np
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,199 @@
+/*
+ * gravmag.h -- C ABI of the GB300 fast BTTB gravity / magnetic operator.
+ *
+ * The library computes the forward product d = G m and the transpose product
+ * m' = G^T d of the sensitivity matrix G of Hogue, Renaut & Vatankhah, "Fast
+ * BTTB forward and transpose operators for 3-D gravity and magnetic data"
+ * (arXiv 1912.06976):
+ *
+ *   Sec. 2 (Eqs. stationsij, prismspqr, Gslice, htilde) -- the geometry: sx * sy
+ *     stations at the centres of the top faces of the unpadded cells, a volume
+ *     of nx * ny * nz prisms with nx = sx + pxl + pxr, ny = sy + pyl + pyr
+ *     (padding of Sec. 2.1.2, Eq. PaddedDistances), z positive down;
+ *   Sec. 4 -- the entries: the gravity prism formula (Sec. 4.1) and the
+ *     induced-magnetisation total-field formula (Sec. 4.2, Eq. magnetickernel);
+ *   Sec. 3 (Eqs. GrviaT, Tcircpadded, Tcircpaddedgeneral, Wpadded, WTpadded,
+ *     Ttran0, Ttran) and Algorithm multbttb -- the products through the
+ *     block-circulant embedding and 2-D FFTs.
+ *
+ * Layouts (Eq. htilde, x fastest):
+ *   model  m[r][q][p]  r < nz, q < ny, p < nx   (n = nx*ny*nz elements)
+ *   data   d[j][i]     j < sy, i < sx           (m = sx*sy elements)
+ * Element type: float for a GM_F32 handle, double for a GM_F64 handle.
+ *
+ * Units: gravity m in g/cm^3 and d in mGal (gamma = 6.67430e-3 mGal per
+ * g/cm^3 per metre); magnetic m = susceptibility (SI) and d = total-field
+ * anomaly in nT for a field of F nT (x North, y East, z down; inclination I
+ * and declination D in degrees, induced magnetisation only).
+ *
+ * Ownership: the handle owns the spectra, the FFT twiddle tables and its
+ * workspace, all allocated by the setup call on the device that is current
+ * then; the caller owns every m / d buffer it passes.  Applies allocate
+ * nothing, do not synchronise (except the *_host variants) and are ordered on
+ * the CUDA stream passed in (NULL = the legacy default stream).  A handle has
+ * one workspace: calls on one handle must not overlap in time (serialise them
+ * on one stream); distinct handles are independent.
+ *
+ * Errors: every call returns a gm_status (setup returns NULL and sets the
+ * thread's last status).  No call faults the process on bad arguments.
+ */
+#ifndef GRAVMAG_H
+#define GRAVMAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GM_API __attribute__((visibility("default")))
+#else
+#define GM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gm_plan *gm_handle;
+
+typedef enum {
+    GM_OK = 0,
+    GM_EINVAL = 1,   /* bad argument: sizes, spacings, pointers, angles, aliasing */
+    GM_ENOMEM = 2,   /* the plan does not fit in free device memory (or the set limit) */
+    GM_ECUDA = 3,    /* a CUDA runtime call failed; the handle stays valid */
+    GM_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+    GM_EDEVICE = 5,  /* a device-side check set the handle's error word */
+    GM_ENODEV = 6    /* no usable CUDA device */
+} gm_status;
+
+typedef enum { GM_GRAVITY = 0, GM_MAGNETIC = 1 } gm_kind;
+typedef enum { GM_F32 = 0, GM_F64 = 1 } gm_precision;
+
+/* Full parameter record for grav_mag_setup_ex.  Sec. 2.1.2 and the parameter
+ * table of App. A: stations, layers, cell sizes, left/right padding in x and y,
+ * depth coordinates (z_blocks), and D, I, F for the magnetic kernel. */
+typedef struct {
+    int sx, sy, nz;         /* stations in x and y (>= 1); depth layers (>= 1)          */
+    int pxl, pxr, pyl, pyr; /* padding cells before / after the stations (>= 0)          */
+    double dx, dy;          /* cell sizes in x and y, metres (> 0)                        */
+    double dz;              /* uniform layer thickness, used when zplanes == NULL (> 0)   */
+    const double *zplanes;  /* optional HOST array of nz + 1 strictly increasing depths
+                               (m) of the layer boundaries, zplanes[0] >= 0 (the stations
+                               are at depth 0; Table of App. A, z_blocks); copied during
+                               the call                                                   */
+    int kind;               /* gm_kind                                                    */
+    double incl_deg;        /* inclination I, |I| <= 90 (magnetic only)                   */
+    double decl_deg;        /* declination D (magnetic only)                              */
+    double F_nT;            /* field intensity F in nT (> 0; magnetic only)               */
+    int precision;          /* gm_precision of the apply path; the setup is always FP64  */
+} gm_params;
+
+/* Set-up (Algorithms symBTTBFFT / BTTBFFT of App. B): evaluates the prism
+ * entries of every depth layer in FP64 on the device, builds the circulant
+ * generators of Eqs. Tcircpadded / Tcircpaddedgeneral and stores their 2-D
+ * FFTs.  nx, ny are the STATION counts s_x, s_y (= unpadded cells); px, py
+ * pad cells on EACH side; dz the uniform layer thickness; kind a gm_kind;
+ * incl_deg, decl_deg are ignored for gravity.  F = 50000 nT, FP32 applies.
+ * Returns NULL on error (see gm_last_status / gm_last_error). */
+GM_API gm_handle grav_mag_setup(int nx, int ny, int nz, double dx, double dy, double dz, int px, int py,
+                         int kind, double incl_deg, double decl_deg);
+
+/* Set-up with the full parameter record (asymmetric padding, variable layer
+ * depths, F, apply precision).  NULL on error. */
+GM_API gm_handle grav_mag_setup_ex(const gm_params *p);
+
+/* Forward product d = G m (Algorithm multbttb, t = 1; Eq. GrviaT with W of
+ * Eq. Wpadded): m_dev is a device array of n elements, d_dev one of m
+ * elements, in the handle's precision; d is overwritten.  m_dev and d_dev
+ * must not overlap (GM_EINVAL).  stream: a cudaStream_t or NULL. */
+GM_API gm_status apply_forward(gm_handle h, const void *m_dev, void *d_dev, void *stream);
+
+/* Transpose product m' = G^T d (Algorithm multbttb, t = 2; Eqs. Ttran0, Ttran
+ * and WTpadded; realised with the complex conjugate of the forward spectra,
+ * which equals the FFT of the index-reversed generator because the
+ * generator is real).  d_dev: m elements, m_dev: n elements, overwritten. */
+GM_API gm_status apply_transpose(gm_handle h, const void *d_dev, void *m_dev, void *stream);
+
+/* The same products from and to HOST buffers: copies the input to the
+ * handle's device staging buffer, applies, copies the result back and
+ * synchronises the stream before returning.  Pinned host memory makes the
+ * copies asynchronous DMA; pageable memory works too. */
+GM_API gm_status apply_forward_host(gm_handle h, const void *m_host, void *d_host, void *stream);
+GM_API gm_status apply_transpose_host(gm_handle h, const void *d_host, void *m_host, void *stream);
+
+/* Releases everything the handle owns (synchronises its device first).
+ * NULL is accepted and returns GM_OK. */
+GM_API gm_status grav_mag_destroy(gm_handle h);
+
+/* Sizes and memory of a plan. */
+typedef struct {
+    int sx, sy, nz, nx, ny;  /* stations, layers and padded cells                        */
+    int fft_nx, fft_ny;      /* FFT lengths N'_x >= sx + nx - 1, N'_y >= sy + ny - 1      */
+    int spec_nx;             /* N'_x / 2 + 1 columns kept of each real-input transform   */
+    int kind, precision;
+    int64_t n_model, n_data; /* n and m                                                   */
+    size_t spectrum_bytes;   /* resident spectra                                          */
+    size_t workspace_bytes;  /* resident workspace (intermediates + host-call staging)    */
+    double setup_ms;         /* device time of the set-up kernels                         */
+} gm_info;
+
+GM_API gm_status gm_get_info(gm_handle h, gm_info *out);
+
+/* Copies the stored spectra to host memory: out holds spec_nx * nz * fft_ny
+ * complex values (interleaved re, im) in the handle's precision, ordered
+ * [kx][r][ky], i.e. the 2-D FFT of layer r's circulant generator at
+ * frequency (kx, ky).  bytes must be at least spectrum_bytes. */
+GM_API gm_status gm_copy_spectrum(gm_handle h, void *host_out, size_t bytes);
+
+/* Smallest even integer >= max(n, 2) whose prime factors are all in
+ * {2, 3, 5, 7}: the FFT length the plan uses per axis for a linear
+ * convolution of support n (any length >= n is exact, Sec. 3).  Host only.
+ * Returns -1 for n < 1 or n > 2^24. */
+GM_API int gm_fft_length(int n);
+
+/* Checks a parameter record without touching the device (GM_OK / GM_EINVAL). */
+GM_API gm_status gm_validate_params(const gm_params *p);
+
+/* Caps the device bytes a set-up may allocate (0 = no cap beyond free
+ * memory); a plan above the cap fails with GM_ENOMEM before allocating. */
+GM_API void gm_set_memory_limit(size_t bytes);
+
+/* Tikhonov-regularised least squares (min ||G x - d||^2 + alpha^2 ||x||^2)
+ * by CGLS: each iteration applies G once and G^T once; the vector updates,
+ * dot products (accumulated in FP64) and step lengths stay on the device, so
+ * the loop never waits for the host.  d_dev: m elements; x0_dev: n elements
+ * or NULL for a zero start; x_dev: n elements, receives the iterate after
+ * `iters` iterations (may equal x0_dev).  resid_host, if not NULL, receives
+ * iters + 1 values of ||G x_k - d||_2 (k = 0..iters; synchronises the stream
+ * at the end).  Scratch: six vectors held by the handle, allocated on the
+ * first call (so the first call is not capturable in a CUDA graph). */
+GM_API gm_status gm_cgls(gm_handle h, const void *d_dev, const void *x0_dev, void *x_dev, double alpha,
+                  int iters, double *resid_host, void *stream);
+
+/* Thread-local status and message of the last failing call of this thread. */
+GM_API gm_status gm_last_status(void);
+GM_API const char *gm_last_error(void);
+GM_API const char *gm_status_string(gm_status s);
+
+/* Number of kernels the last apply / CGLS call on this handle launched. */
+GM_API int gm_last_launch_count(gm_handle h);
+
+/* Per-kernel device timing of the handle's own launches (tracing).  While
+ * enabled with a capacity > 0, every kernel the handle launches is bracketed by
+ * two CUDA events recorded on the launching stream (up to `capacity` launches;
+ * later launches run untimed).  gm_kernel_times synchronises those events and
+ * returns, per kernel, its launch count and summed device time since the last
+ * query (then resets).  capacity = 0 disables timing and frees the events. */
+typedef struct {
+    char name[32];  /* kernel name, e.g. "fwd_cols_mac" */
+    int launches;
+    double total_ms;
+} gm_kernel_time;
+
+GM_API gm_status gm_enable_timing(gm_handle h, int capacity);
+GM_API int gm_kernel_times(gm_handle h, gm_kernel_time *out, int max_entries);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAVMAG_H */

@@ -100,8 +100,9 @@ class Geometry:
     sx, sy  stations in x and y (= unpadded cells per row / column)
     nz      depth layers
     pxl, pxr, pyl, pyr  padding cells left/right of the stations in x and y
-    dx, dy  cell sizes (m); zplanes: nz+1 increasing depths (m), z down,
-            zplanes[0] the station level (uniform layers: k*dz)
+    dx, dy  cell sizes (m); zplanes: nz+1 increasing layer boundaries (m),
+            z down, zplanes[0] >= 0; the stations are at depth 0 (uniform
+            layers: k*dz)
     kind    GRAVITY (m in g/cm^3, d in mGal) or MAGNETIC (m = susceptibility
             SI, d in nT; x North, y East)
     """

@@ -26,7 +26,8 @@
  *     b_j = (j + pyl + 1/2) dy;
  *   cells (p, q, r), 0 <= p < nx = sx + pxl + pxr, 0 <= q < ny, 0 <= r < nz,
  *     spanning [p dx, (p+1) dx] x [q dy, (q+1) dy] x [z_r, z_{r+1}];
- *   z positive down; z_0 is the station level.
+ *   z positive down; the stations are at depth 0 and the layer boundaries
+ *   z_0 < z_1 < ... < z_nz (z_0 >= 0) are given (z_blocks of App. A).
  *   Row index of G:    k = j*sx + i        (x fastest, Eq. htilde)
  *   Column index of G: l = (r*ny + q)*nx + p
  *
@@ -75,7 +76,7 @@ typedef struct {
     int sx, sy, nz;
     int pxl, pxr, pyl, pyr;
     double dx, dy;
-    const double *zplanes; /* nz + 1 increasing depths; zplanes[0] is the station level */
+    const double *zplanes; /* nz + 1 increasing layer boundaries (m), zplanes[0] >= 0 */
     int kind;              /* GMO_GRAVITY or GMO_MAGNETIC */
     double incl_deg, decl_deg, F_nT;
 } gmo_geom;
@@ -176,8 +177,8 @@ static ld entry_ld(const gmo_geom *g, const ld mc[5], int i, int j, int p, int q
     ld x2 = x1 + (ld)g->dx;
     ld y1 = ((ld)(q - j - g->pyl) - 0.5L) * (ld)g->dy;
     ld y2 = y1 + (ld)g->dy;
-    ld z1 = (ld)g->zplanes[r] - (ld)g->zplanes[0];
-    ld z2 = (ld)g->zplanes[r + 1] - (ld)g->zplanes[0];
+    ld z1 = (ld)g->zplanes[r];
+    ld z2 = (ld)g->zplanes[r + 1];
     if (g->kind == GMO_GRAVITY) return GMO_GAMMA * grav_prism_ld(x1, x2, y1, y2, z1, z2);
     ld t[6];
     mag_terms_ld(x1, x2, y1, y2, z1, z2, t);

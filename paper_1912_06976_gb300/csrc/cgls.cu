@@ -1,0 +1,222 @@
+// cgls.cu -- Tikhonov-regularised CGLS with every step on the device.
+//
+// Solves min ||G x - d||^2 + alpha^2 ||x||^2 with the conjugate-gradient method
+// on the normal equations (G^T G + alpha^2 I) x = G^T d, in its least-squares
+// form (CGLS): per iteration one forward and one transpose product of the
+// fast operator (the use the paper's conclusion names for the transpose
+// product, Sec. 7) plus the vector updates below.  Scalars (gamma, delta, the
+// step lengths) live in device memory, dot products are accumulated in FP64
+// with a fixed two-stage reduction (bit-reproducible), and no iteration waits
+// for the host.
+//
+//   r = d - G x0;  s = G^T r - alpha^2 x0;  p = s;  gamma = ||s||^2
+//   repeat: q = G p;  delta = ||q||^2 + alpha^2 ||p||^2;  a = gamma / delta
+//           x += a p;  r -= a q;  s = G^T r - alpha^2 x
+//           gamma' = ||s||^2;  b = gamma' / gamma;  gamma = gamma';  p = s + b p
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "gm_plan.h"
+
+namespace gm {
+
+constexpr int kRedBlocks = 512;
+constexpr int kRedThreads = 256;
+
+// scalar slots
+enum { S_GAMMA = 0, S_A = 1, S_B = 2, S_ALPHA2 = 3, S_COUNT = 8 };
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    return v;
+}
+
+// part[blk] = partial SUM a[i]^2 (i < na); part[kRedBlocks + blk] = partial SUM b[i]^2 (i < nb)
+template <typename R>
+__global__ void k_sumsq2(const R *__restrict__ a, size_t na, const R *__restrict__ b, size_t nb, double *part) {
+    __shared__ double sh[32];
+    double sa = 0, sb = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < na; i += (size_t)gridDim.x * blockDim.x)
+        sa += (double)a[i] * (double)a[i];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nb; i += (size_t)gridDim.x * blockDim.x)
+        sb += (double)b[i] * (double)b[i];
+    sa = block_sum(sa, sh);
+    sb = block_sum(sb, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = sa;
+        part[kRedBlocks + blockIdx.x] = sb;
+    }
+}
+
+__device__ double sum_parts(const double *part, double *sh) {
+    double v = 0;
+    for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) v += part[i];
+    return block_sum(v, sh);
+}
+
+// init: gamma = ||s||^2 (parts[0..]); resid[0] = sqrt(||r||^2) (parts[K..])
+__global__ void k_init_scalars(const double *part, double *sc, double *resid, double alpha2) {
+    __shared__ double sh[32];
+    double s2 = sum_parts(part, sh);
+    double r2 = sum_parts(part + kRedBlocks, sh);
+    if (threadIdx.x == 0) {
+        sc[S_GAMMA] = s2;
+        sc[S_ALPHA2] = alpha2;
+        resid[0] = sqrt(r2);
+    }
+}
+
+// a = gamma / (||q||^2 + alpha^2 ||p||^2)
+__global__ void k_step_length(const double *part, double *sc) {
+    __shared__ double sh[32];
+    double q2 = sum_parts(part, sh);
+    double p2 = sum_parts(part + kRedBlocks, sh);
+    if (threadIdx.x == 0) {
+        double delta = q2 + sc[S_ALPHA2] * p2;
+        sc[S_A] = (delta > 0) ? sc[S_GAMMA] / delta : 0.0;
+    }
+}
+
+// b = gamma' / gamma, gamma = gamma'; resid[k] = ||r||
+__global__ void k_beta(const double *part, double *sc, double *resid, int k) {
+    __shared__ double sh[32];
+    double s2 = sum_parts(part, sh);
+    double r2 = sum_parts(part + kRedBlocks, sh);
+    if (threadIdx.x == 0) {
+        double g = sc[S_GAMMA];
+        sc[S_B] = (g > 0) ? s2 / g : 0.0;
+        sc[S_GAMMA] = s2;
+        resid[k] = sqrt(r2);
+    }
+}
+
+// r = d - r (r holds G x0 on entry)
+template <typename R>
+__global__ void k_residual0(const R *__restrict__ d, R *__restrict__ r, size_t m) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
+        r[i] = d[i] - r[i];
+}
+
+// s -= alpha^2 x; p = s (when set_p)
+template <typename R>
+__global__ void k_s_update(R *__restrict__ s, const R *__restrict__ x, R *__restrict__ p, size_t n, R a2, int set_p) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        R v = s[i] - a2 * x[i];
+        s[i] = v;
+        if (set_p) p[i] = v;
+    }
+}
+
+// x += a p (i < n); r -= a q (i < m)
+template <typename R>
+__global__ void k_update_xr(R *__restrict__ x, const R *__restrict__ p, size_t n, R *__restrict__ r,
+                            const R *__restrict__ q, size_t m, const double *sc) {
+    const R a = (R)sc[S_A];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        x[i] += a * p[i];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
+        r[i] -= a * q[i];
+}
+
+// p = s + b p
+template <typename R>
+__global__ void k_update_p(R *__restrict__ p, const R *__restrict__ s, size_t n, const double *sc) {
+    const R b = (R)sc[S_B];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = s[i] + b * p[i];
+}
+
+template <typename R>
+static cudaError_t cgls_t(gm_plan *p, const R *d, const R *x0, R *x, double alpha, int iters, double *resid_host,
+                          cudaStream_t st, int *nl) {
+    const size_t n = (size_t)p->geo.nx * p->geo.ny * p->geo.nz, m = (size_t)p->geo.sx * p->geo.sy;
+    const size_t vec = sizeof(R) * (2 * n + 2 * m);
+    const size_t need = vec + sizeof(double) * (2 * kRedBlocks + S_COUNT + (size_t)iters + 1) + 256;
+    if (need > p->cgls_bytes) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        cudaFree(p->cgls_buf);
+        p->cgls_buf = nullptr;
+        p->cgls_bytes = 0;
+        e = cudaMalloc(&p->cgls_buf, need);
+        if (e != cudaSuccess) return e;
+        p->cgls_bytes = need;
+    }
+    char *base = static_cast<char *>(p->cgls_buf);
+    R *s = reinterpret_cast<R *>(base);
+    R *pv = s + n;
+    R *r = pv + n;
+    R *q = r + m;
+    double *part = reinterpret_cast<double *>(base + ((sizeof(R) * (2 * n + 2 * m) + 255) / 256) * 256);
+    double *sc = part + 2 * kRedBlocks;
+    double *resid = sc + S_COUNT;
+    int launches = 0, k = 0;
+    cudaError_t e = cudaSuccess;
+    const int vb = kRedBlocks, vt = kRedThreads;
+#define CG_TRY(x)                                  \
+    do {                                           \
+        e = (x);                                   \
+        if (e != cudaSuccess) goto out;            \
+    } while (0)
+    if (x0 && x0 != x) CG_TRY(cudaMemcpyAsync(x, x0, sizeof(R) * n, cudaMemcpyDeviceToDevice, st));
+    if (!x0) CG_TRY(cudaMemsetAsync(x, 0, sizeof(R) * n, st));
+    {
+        int l = 0;
+        CG_TRY(launch_forward(p, x, r, st, &l));  // r = G x0
+        launches += l;
+    }
+    k_residual0<R><<<vb, vt, 0, st>>>(d, r, m);
+    {
+        int l = 0;
+        CG_TRY(launch_transpose(p, r, s, st, &l));  // s = G^T r
+        launches += l;
+    }
+    k_s_update<R><<<vb, vt, 0, st>>>(s, x, pv, n, (R)(alpha * alpha), 1);
+    k_sumsq2<R><<<vb, vt, 0, st>>>(s, n, r, m, part);
+    k_init_scalars<<<1, 1024, 0, st>>>(part, sc, resid, alpha * alpha);
+    launches += 4;
+    for (k = 1; k <= iters; ++k) {
+        int l = 0;
+        CG_TRY(launch_forward(p, pv, q, st, &l));  // q = G p
+        launches += l;
+        k_sumsq2<R><<<vb, vt, 0, st>>>(q, m, pv, n, part);
+        k_step_length<<<1, 1024, 0, st>>>(part, sc);
+        k_update_xr<R><<<vb, vt, 0, st>>>(x, pv, n, r, q, m, sc);
+        CG_TRY(launch_transpose(p, r, s, st, &l));  // s = G^T r
+        launches += l;
+        k_s_update<R><<<vb, vt, 0, st>>>(s, x, pv, n, (R)(alpha * alpha), 0);
+        k_sumsq2<R><<<vb, vt, 0, st>>>(s, n, r, m, part);
+        k_beta<<<1, 1024, 0, st>>>(part, sc, resid, k);
+        k_update_p<R><<<vb, vt, 0, st>>>(pv, s, n, sc);
+        launches += 6;
+        CG_TRY(cudaGetLastError());
+    }
+    CG_TRY(cudaGetLastError());
+    if (resid_host) {
+        CG_TRY(cudaMemcpyAsync(resid_host, resid, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost, st));
+        CG_TRY(cudaStreamSynchronize(st));
+    }
+out:
+#undef CG_TRY
+    *nl = launches;
+    return e;
+}
+
+cudaError_t run_cgls(gm_plan *p, const void *d, const void *x0, void *x, double alpha, int iters, double *resid_host,
+                     cudaStream_t s, int *nl) {
+    if (p->precision == GM_F64)
+        return cgls_t<double>(p, static_cast<const double *>(d), static_cast<const double *>(x0),
+                              static_cast<double *>(x), alpha, iters, resid_host, s, nl);
+    return cgls_t<float>(p, static_cast<const float *>(d), static_cast<const float *>(x0), static_cast<float *>(x),
+                         alpha, iters, resid_host, s, nl);
+}
+
+}  // namespace gm

@@ -1,0 +1,111 @@
+// gm_common.cuh -- types and device helpers shared by the set-up and apply kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gm {
+
+// Complex type of a real precision.
+template <typename R> struct cpx_of;
+template <> struct cpx_of<float> { using type = float2; };
+template <> struct cpx_of<double> { using type = double2; };
+template <typename R> using cpx_t = typename cpx_of<R>::type;
+
+template <typename C> __device__ __forceinline__ C c_make(decltype(C::x) x, decltype(C::x) y) {
+    C c; c.x = x; c.y = y; return c;
+}
+template <typename C> __device__ __forceinline__ C c_add(C a, C b) { return c_make<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C c_sub(C a, C b) { return c_make<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C c_mul(C a, C b) {
+    return c_make<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C c_mulc(C a, C b) {
+    return c_make<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C> __device__ __forceinline__ C c_conj(C a) { return c_make<C>(a.x, -a.y); }
+
+// Opts a kernel into more than the default 48 KB of dynamic shared memory when needed.
+template <typename K>
+inline cudaError_t allow_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Mixed-radix plan of one FFT length: the radices of its passes (product = N)
+// and a table of the N roots exp(-2 pi i e / N), e < N, in the kernel's precision.
+constexpr int kMaxPasses = 16;
+struct FftDesc {
+    int N;
+    int npass;
+    int radix[kMaxPasses];
+    const void *tw;
+};
+
+// Geometry of a plan as the kernels see it.
+struct Geo {
+    int sx, sy, nz, nx, ny;     // stations, layers, padded cells
+    int pxl, pyl;               // left padding
+    int NPx, NPy, Kx;           // FFT lengths, kept x-columns N'_x/2+1
+};
+
+// Batched in-place-ish Stockham autosort FFT on shared memory, all threads of
+// the block cooperating.  nb transforms of length d.N live at buf0 + t*ld
+// (t < nb); buf1 is scratch of the same shape.  Each pass of radix R maps
+// input j + rr*(N/R) to output (j / Ns)*Ns*R + (j mod Ns) + s*Ns after the
+// twiddle W_{Ns R}^{rr (j mod Ns)} and an R-point DFT (Ns = product of the
+// earlier radices), so the result comes out in natural order.  Returns the
+// buffer that holds the result.  inverse = unnormalised inverse transform.
+// The caller synchronises the block before the call; the call ends synchronised.
+template <typename C>
+__device__ C *fft_block(C *buf0, C *buf1, int nb, int ld, const FftDesc &d, bool inverse) {
+    const C *tw = reinterpret_cast<const C *>(d.tw);
+    const int N = d.N;
+    C *src = buf0, *dst = buf1;
+    int Ns = 1;
+    for (int ps = 0; ps < d.npass; ++ps) {
+        const int R = d.radix[ps];
+        const int M = N / R;
+        const int step = N / (Ns * R);
+        for (int item = threadIdx.x; item < nb * M; item += blockDim.x) {
+            const int t = item / M;
+            const int j = item - t * M;
+            const int k = j % Ns;
+            C v[8], o[8];
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr)
+                if (rr < R) v[rr] = src[t * ld + j + rr * M];
+#pragma unroll
+            for (int rr = 1; rr < 8; ++rr)
+                if (rr < R) {
+                    C w = tw[(rr * k * step) % N];
+                    if (inverse) w.y = -w.y;
+                    v[rr] = c_mul(v[rr], w);
+                }
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                if (s < R) {
+                    C acc = v[0];
+#pragma unroll
+                    for (int rr = 1; rr < 8; ++rr)
+                        if (rr < R) {
+                            C w = tw[((rr * s) % R) * M];
+                            if (inverse) w.y = -w.y;
+                            acc = c_add(acc, c_mul(v[rr], w));
+                        }
+                    o[s] = acc;
+                }
+            const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                if (s < R) dst[t * ld + base + s * Ns] = o[s];
+        }
+        __syncthreads();
+        C *tmp = src; src = dst; dst = tmp;
+        Ns *= R;
+    }
+    return src;
+}
+
+}  // namespace gm

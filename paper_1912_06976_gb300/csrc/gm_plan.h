@@ -1,0 +1,92 @@
+// gm_plan.h -- host-side plan record and the launchers each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gravmag.h"
+#include "gm_common.cuh"
+
+struct gm_plan {
+    int device = 0;
+    int kind = GM_GRAVITY;
+    int precision = GM_F32;
+    gm::Geo geo{};
+    int pxr = 0, pyr = 0;
+    int Nx = 0, Ny = 0;  // linear-convolution supports sx+nx-1, sy+ny-1
+    double dx = 0, dy = 0;
+    std::vector<double> zplanes;
+    double incl_deg = 90, decl_deg = 0, F_nT = 50000;
+    double coef[5] = {0, 0, 0, 0, 0};  // magnetic: F/4pi-scaled coefficients of {Lx, Ly, Lz, Ax, Ay}
+
+    // FFT plans (radix lists) and device twiddle tables in the apply precision.
+    gm::FftDesc fx{}, fy{};
+    void *tw_x = nullptr, *tw_y = nullptr;
+
+    // Spectra [Kx][nz][NPy], complex in the apply precision.
+    void *spec = nullptr;
+    size_t spec_bytes = 0;
+
+    // Workspace: the large intermediate (forward [Kx][nz][ny], transpose [nz][ny][Kx]),
+    // the small one (forward [sy][Kx], transpose [Kx][sy]) and host-call staging.
+    void *work_big = nullptr, *work_small = nullptr;
+    void *stage_m = nullptr, *stage_d = nullptr;
+    size_t work_bytes = 0;
+
+    // CGLS scratch, allocated on the first gm_cgls call.
+    void *cgls_buf = nullptr;
+    size_t cgls_bytes = 0;
+
+    double setup_ms = 0;
+    int last_launches = 0;
+
+    // Optional per-kernel timing: event pairs around each launch (see gm_enable_timing).
+    std::vector<cudaEvent_t> tev;   // 2 per slot
+    std::vector<int> tkid;          // kernel id per used slot
+    int tused = 0;
+};
+
+namespace gm {
+// Kernel ids for the timing table.
+enum KernelId {
+    K_FWD_ROWS = 0, K_FWD_COLS = 1, K_FWD_C2R = 2, K_TR_ROWS = 3, K_TR_COLS = 4, K_TR_C2R = 5, K_CGLS_VEC = 6,
+    K_COUNT = 7
+};
+extern const char *const kKernelNames[K_COUNT];
+
+// Records the "before" event of a timed launch; returns the slot or -1.
+inline int timing_begin(gm_plan *p, cudaStream_t s, int kid) {
+    if (p->tused >= (int)p->tkid.size()) return -1;
+    int slot = p->tused++;
+    p->tkid[slot] = kid;
+    cudaEventRecord(p->tev[2 * slot], s);
+    return slot;
+}
+inline void timing_end(gm_plan *p, cudaStream_t s, int slot) {
+    if (slot >= 0) cudaEventRecord(p->tev[2 * slot + 1], s);
+}
+}  // namespace gm
+
+namespace gm {
+
+// Radix list of N (8s, then 4, 2, 3, 5, 7); false if N has another prime factor.
+bool make_radices(int N, FftDesc &d);
+
+// Twiddle table exp(-2 pi i e / N), e < N, computed on the host in long double
+// and rounded to the element type; allocated on the device.
+cudaError_t make_twiddles(int N, bool f64, void **dev_out);
+
+// Set-up: FP64 entries -> generators -> FP64 2-D FFT -> spectra in the plan's precision.
+cudaError_t build_spectra(gm_plan *p, cudaStream_t s);
+
+// Apply launchers (forward: K4-K6, transpose: K7-K9); return the launch count in *nl.
+cudaError_t launch_forward(gm_plan *p, const void *m, void *d, cudaStream_t s, int *nl);
+cudaError_t launch_transpose(gm_plan *p, const void *d, void *m, cudaStream_t s, int *nl);
+
+// CGLS on the device (cgls.cu).
+cudaError_t run_cgls(gm_plan *p, const void *d, const void *x0, void *x, double alpha, int iters,
+                     double *resid_host, cudaStream_t s, int *nl);
+
+}  // namespace gm

@@ -1,0 +1,207 @@
+// setup.cu -- set-up of a plan: prism entries in FP64, circulant generators, spectra.
+//
+// Algorithms symBTTBFFT / BTTBFFT (App. B) with the gravity and magnetic
+// entry functions of Sec. 4, re-organised for the device:
+//
+//  K1 k_corner_columns: for every layer r and every corner (x_a, y_b) of the
+//     offset grid (Eq. PaddedDistances: x_a = (a + dmin_x - 1/2) dx, a <= N_x),
+//     Q_r(x, y) = Phi(x, y, z_{r+1}) - Phi(x, y, z_r), the depth difference of
+//     the corner function.  As in the paper's simplification (Sec. 4.1, Eq.
+//     simplifiedCMX: ln((x+R1)/(x+R2)) instead of two logs), the difference is
+//     taken inside the logarithms and arctangents, here in forms with no
+//     cancellation (log1p of the relative increment, atan of the tangent of the
+//     angle difference), which keeps far-field entries accurate in FP64.
+//  K2 k_generator: the 4-point difference over the corners of each cell offset
+//     gives the entry k_r(delta) (Sec. 4.1: g = CM(1:,1:) - CM(1:,2:) - ...);
+//     entry k_r(delta) with delta = -u - pxl is written at generator position
+//     (u mod N'_x, v mod N'_y) for u in [-(nx-1), sx-1] (Eqs. Tcircpadded,
+//     Tcircpaddedgeneral), zeros elsewhere.
+//  K3 2-D FFT of each generator in FP64 (rows, then columns), then rounding
+//     to the apply precision.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "gm_kernels.cuh"
+#include "gm_plan.h"
+
+namespace gm {
+
+// ln(rho2 + a) - ln(rho1 + a) with rho_k = sqrt(a^2 + b2 + z_k^2), z2 > z1 >= 0.
+__device__ __forceinline__ double dlog_rho_plus(double a, double b2, double z1, double z2, double r1,
+                                                double r2) {
+    const double dz2 = (z2 - z1) * (z2 + z1);
+    const double drho = dz2 / (r1 + r2);
+    if (a >= 0.0) return log1p(drho / (a + r1));
+    // rho_k + a = (b2 + z_k^2) / (rho_k - a)
+    return log1p(dz2 / (b2 + z1 * z1)) - log1p(drho / (r1 - a));
+}
+
+// Gravity: Phi = z atan(x y / (z rho)) - x ln(rho + y) - y ln(rho + x) (Sec. 4.1).
+__device__ double q_gravity(double x, double y, double z1, double z2) {
+    const double R2 = x * x + y * y;
+    const double r1 = sqrt(R2 + z1 * z1), r2 = sqrt(R2 + z2 * z2);
+    double at;
+    if (z1 == 0.0) {
+        at = z2 * atan(x * y / (z2 * r2));
+    } else {
+        // atan(c2) - atan(c1) = atan((c2 - c1) / (1 + c1 c2)), c_k = x y / (z_k rho_k) of one sign
+        const double num = -x * y * (z2 - z1) * (z2 + z1) * (R2 + z1 * z1 + z2 * z2);
+        const double den = (z2 * r2 + z1 * r1) * (z1 * z2 * r1 * r2 + x * x * y * y);
+        at = z2 * atan(num / den) + (z2 - z1) * atan(x * y / (z1 * r1));
+    }
+    return at - x * dlog_rho_plus(y, x * x, z1, z2, r1, r2) - y * dlog_rho_plus(x, y * y, z1, z2, r1, r2);
+}
+
+// Magnetic (Sec. 4.2, Eq. magnetickernel): c . {dLx, dLy, dLz, dAx, dAy}.
+__device__ double q_magnetic(double x, double y, double z1, double z2, const double c[5]) {
+    const double R2 = x * x + y * y;
+    const double r1 = sqrt(R2 + z1 * z1), r2 = sqrt(R2 + z2 * z2);
+    const double dz2 = (z2 - z1) * (z2 + z1);
+    const double Lx = dlog_rho_plus(x, y * y, z1, z2, r1, r2);
+    const double Ly = dlog_rho_plus(y, x * x, z1, z2, r1, r2);
+    const double Lz = log1p((z2 - z1 + dz2 / (r1 + r2)) / (z1 + r1));
+    // atan(a2) - atan(a1) with a_k = y z_k / (x rho_k) (one sign): atan((a2-a1)/(1+a1 a2))
+    const double k = x * y * R2 * dz2 / (z2 * r1 + z1 * r2);
+    const double Ax = atan(k / (x * x * r1 * r2 + y * y * z1 * z2));
+    const double Ay = atan(k / (y * y * r1 * r2 + x * x * z1 * z2));
+    return c[0] * Lx + c[1] * Ly + c[2] * Lz + c[3] * Ax + c[4] * Ay;
+}
+
+struct CornerArgs {
+    int ncx, ncy, nz;     // corners per axis (N_x + 1, N_y + 1), layers
+    double x0, y0;        // coordinate of corner 0 (metres)
+    double dx, dy;
+    const double *z;      // nz + 1 depths (device)
+    int kind;
+    double c[5];          // magnetic coefficients, or {gamma} for gravity
+};
+
+// K1: Q[r][b][a] for a < ncx, b < ncy, r < nz.
+__global__ void k_corner_columns(double *__restrict__ Q, CornerArgs a) {
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y;
+    const int r = blockIdx.z;
+    if (ix >= a.ncx) return;
+    const double x = a.x0 + ix * a.dx;
+    const double y = a.y0 + iy * a.dy;
+    const double z1 = a.z[r], z2 = a.z[r + 1];
+    double q = (a.kind == GM_GRAVITY) ? a.c[0] * q_gravity(x, y, z1, z2) : q_magnetic(x, y, z1, z2, a.c);
+    Q[((size_t)r * a.ncy + iy) * a.ncx + ix] = q;
+}
+
+// K2: generator T[r][vy][ux] (real, FP64) from the corner columns.
+__global__ void k_generator(const double *__restrict__ Q, double *__restrict__ T, Geo g, int ncx, int ncy) {
+    const int ux = blockIdx.x * blockDim.x + threadIdx.x;
+    const int vy = blockIdx.y;
+    const int r = blockIdx.z;
+    if (ux >= g.NPx) return;
+    const int u = (ux < g.sx) ? ux : ux - g.NPx;
+    const int v = (vy < g.sy) ? vy : vy - g.NPy;
+    double t = 0.0;
+    if (u >= -(g.nx - 1) && v >= -(g.ny - 1)) {
+        // corner index of the lower x edge of offset delta_x = -u - pxl:  sx - 1 - u
+        const int xi = g.sx - 1 - u, yi = g.sy - 1 - v;
+        const double *Qr = Q + (size_t)r * ncy * ncx;
+        t = Qr[(size_t)(yi + 1) * ncx + xi + 1] - Qr[(size_t)(yi + 1) * ncx + xi] -
+            Qr[(size_t)yi * ncx + xi + 1] + Qr[(size_t)yi * ncx + xi];
+    }
+    T[((size_t)r * g.NPy + vy) * g.NPx + ux] = t;
+}
+
+__global__ void k_round_to_f32(const double2 *__restrict__ in, float2 *__restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+#define GM_TRY(x)                              \
+    do {                                       \
+        cudaError_t e_ = (x);                  \
+        if (e_ != cudaSuccess) { err = e_; goto done; } \
+    } while (0)
+
+cudaError_t build_spectra(gm_plan *p, cudaStream_t s) {
+    const Geo &g = p->geo;
+    const int ncx = p->Nx + 1, ncy = p->Ny + 1;
+    cudaError_t err = cudaSuccess;
+    double *z = nullptr, *Q = nullptr, *T = nullptr;
+    double2 *S64 = nullptr;
+    void *tw64x = nullptr, *tw64y = nullptr;
+    FftDesc fx64 = p->fx, fy64 = p->fy;
+    const size_t nspec = (size_t)g.Kx * g.nz * g.NPy;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GM_TRY(cudaEventCreate(&e0));
+    GM_TRY(cudaEventCreate(&e1));
+    GM_TRY(cudaEventRecord(e0, s));
+    GM_TRY(cudaMalloc(&z, sizeof(double) * (g.nz + 1)));
+    GM_TRY(cudaMemcpyAsync(z, p->zplanes.data(), sizeof(double) * (g.nz + 1), cudaMemcpyHostToDevice, s));
+    GM_TRY(cudaMalloc(&Q, sizeof(double) * (size_t)ncx * ncy * g.nz));
+    GM_TRY(cudaMalloc(&T, sizeof(double) * (size_t)g.NPx * g.NPy * g.nz));
+    GM_TRY(cudaMalloc(&S64, sizeof(double2) * nspec));
+    if (p->precision == GM_F64) {
+        tw64x = p->tw_x;
+        tw64y = p->tw_y;
+    } else {
+        GM_TRY(make_twiddles(g.NPx, true, &tw64x));
+        GM_TRY(make_twiddles(g.NPy, true, &tw64y));
+    }
+    fx64.tw = tw64x;
+    fy64.tw = tw64y;
+    {
+        CornerArgs a;
+        a.ncx = ncx; a.ncy = ncy; a.nz = g.nz;
+        a.x0 = ((double)(-(g.sx - 1 + g.pxl)) - 0.5) * p->dx;
+        a.y0 = ((double)(-(g.sy - 1 + g.pyl)) - 0.5) * p->dy;
+        a.dx = p->dx; a.dy = p->dy; a.z = z; a.kind = p->kind;
+        for (int k = 0; k < 5; ++k) a.c[k] = p->coef[k];
+        dim3 blk(128), grd((ncx + 127) / 128, ncy, g.nz);
+        k_corner_columns<<<grd, blk, 0, s>>>(Q, a);
+        GM_TRY(cudaGetLastError());
+    }
+    {
+        dim3 blk(128), grd((g.NPx + 127) / 128, g.NPy, g.nz);
+        k_generator<<<grd, blk, 0, s>>>(Q, T, g, ncx, ncy);
+        GM_TRY(cudaGetLastError());
+    }
+    {
+        // rows: T[r][vy][0:NPx] -> S64[kx][r][vy]
+        dim3 grd((g.NPy + 1) / 2, g.nz);
+        size_t sm = 2 * sizeof(double2) * g.NPx;
+        GM_TRY(allow_smem(k_rows_r2c<double2, double>, sm));
+        GM_TRY(allow_smem(k_cols_fft<double2>, 2 * sizeof(double2) * g.NPy));
+        k_rows_r2c<double2, double><<<grd, 256, sm, s>>>(T, g.NPy, g.NPx, g.nz, S64, g.NPy, fx64, g.Kx);
+        GM_TRY(cudaGetLastError());
+        dim3 grd2(g.Kx, g.nz);
+        size_t sm2 = 2 * sizeof(double2) * g.NPy;
+        k_cols_fft<double2><<<grd2, 256, sm2, s>>>(S64, g.nz, g.NPy, fy64);
+        GM_TRY(cudaGetLastError());
+    }
+    if (p->precision == GM_F64) {
+        GM_TRY(cudaMemcpyAsync(p->spec, S64, sizeof(double2) * nspec, cudaMemcpyDeviceToDevice, s));
+    } else {
+        k_round_to_f32<<<1024, 256, 0, s>>>(S64, reinterpret_cast<float2 *>(p->spec), nspec);
+        GM_TRY(cudaGetLastError());
+    }
+    GM_TRY(cudaEventRecord(e1, s));
+    GM_TRY(cudaStreamSynchronize(s));
+    {
+        float ms = 0;
+        GM_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        p->setup_ms = ms;
+    }
+done:
+    cudaStreamSynchronize(s);
+    cudaFree(z);
+    cudaFree(Q);
+    cudaFree(T);
+    cudaFree(S64);
+    if (p->precision != GM_F64) {
+        cudaFree(tw64x);
+        cudaFree(tw64y);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return err;
+}
+
+}  // namespace gm

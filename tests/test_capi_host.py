@@ -1,0 +1,103 @@
+"""The C ABI on the host (no GPU needed): the library builds and loads, exports
+every function include/gravmag.h declares, and its host-only logic (FFT length
+choice, parameter validation, no-device behaviour) is right."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1912_06976_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    from paper_1912_06976_gb300 import gravmag
+
+    return gravmag
+
+
+def _declared_functions():
+    txt = open(os.path.join(ROOT, "include", "gravmag.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return re.findall(r"^GM_API\s+[\w\s\*]*?\b(\w+)\s*\(", txt, flags=re.M)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("grav_mag_setup", "grav_mag_setup_ex", "apply_forward", "apply_transpose",
+                     "grav_mag_destroy", "gm_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = ctypes.CDLL(B.LIB)
+    missing = [n for n in _declared_functions() if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def _smooth_even(n):
+    m = max(n, 2)
+    while True:
+        if m % 2 == 0:
+            k = m
+            for p in (2, 3, 5, 7):
+                while k % p == 0:
+                    k //= p
+            if k == 1:
+                return m
+        m += 1
+
+
+def test_fft_length_is_smallest_even_7_smooth(lib):
+    for n in list(range(1, 300)) + [549, 659, 1000, 2047, 4097]:
+        assert lib.fft_length(n) == _smooth_even(n)
+    assert lib.fft_length(659) == 672 and lib.fft_length(549) == 560  # the 300x250 grid, 10 % padding
+    assert lib.fft_length(0) == -1
+
+
+@pytest.mark.parametrize("field,value", [("sx", 0), ("nz", 0), ("pxl", -1), ("dx", 0.0), ("dy", -1.0),
+                                         ("kind", 7), ("precision", 3)])
+def test_validate_rejects_bad_fields(lib, field, value):
+    p, keep = lib.make_params(8, 8, 4, 10.0, 10.0, 10.0)
+    lib.validate(p)
+    setattr(p, field, value)
+    with pytest.raises(lib.GravMagError) as e:
+        lib.validate(p)
+    assert e.value.status == lib.GM_EINVAL
+
+
+def test_validate_magnetic_angles_and_zplanes(lib):
+    p, keep = lib.make_params(8, 8, 2, 10.0, 10.0, kind=lib.MAGNETIC, incl_deg=91.0, zplanes=[0, 5, 9])
+    with pytest.raises(lib.GravMagError):
+        lib.validate(p)
+    p, keep = lib.make_params(8, 8, 2, 10.0, 10.0, kind=lib.MAGNETIC, incl_deg=60.0, zplanes=[0, 5, 5])
+    with pytest.raises(lib.GravMagError):
+        lib.validate(p)
+    p, keep = lib.make_params(8, 8, 2, 10.0, 10.0, kind=lib.MAGNETIC, incl_deg=60.0, zplanes=[2, 5, 9])
+    lib.validate(p)
+    p, keep = lib.make_params(3000, 8, 2, 10.0, 10.0, 10.0)  # 2*3000-1 > the single-CTA FFT limit
+    with pytest.raises(lib.GravMagError):
+        lib.validate(p)
+
+
+def test_status_strings(lib):
+    so = lib.load()
+    for s in range(7):
+        assert so.gm_status_string(s).startswith(b"GM_")
+
+
+def test_setup_without_a_device_fails_cleanly(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    so = lib.load()
+    h = so.grav_mag_setup(8, 8, 2, 10.0, 10.0, 10.0, 0, 0, 0, 0.0, 0.0)
+    assert not h
+    assert so.gm_last_status() == lib.GM_ENODEV
+    assert so.apply_forward(None, None, None, None) == lib.GM_EINVAL
+    assert so.grav_mag_destroy(None) == lib.GM_OK

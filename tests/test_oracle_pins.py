@@ -66,7 +66,7 @@ def _cell_bounds(geom, i, j, p, q, r):
     b = (j + geom.pyl + 0.5) * geom.dy
     return ((p * geom.dx - a, (p + 1) * geom.dx - a),
             (q * geom.dy - b, (q + 1) * geom.dy - b),
-            (geom.zplanes[r] - geom.zplanes[0], geom.zplanes[r + 1] - geom.zplanes[0]))
+            (geom.zplanes[r], geom.zplanes[r + 1]))
 
 
 # ---------------------------------------------------------------- P1 point mass

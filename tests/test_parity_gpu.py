@@ -1,0 +1,215 @@
+"""GPU products against the CPU oracle (the parity gate).
+
+FP64 applies must match the long-double dense oracle to a relative 2-norm error
+of 1e-12, FP32 applies to 1e-5 (the paper's measure, Sec. 5).  Small cases are
+compared element by element over the whole vector; the large workloads at
+sampled stations / cells the oracle computes one by one (stored by
+tests/golden/make_golden.py, which calls only the oracle).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1912_06976_gb300 import workloads as W
+from tests.conftest import rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = {1: 1e-12, 0: 1e-5}  # precision -> relative 2-norm tolerance
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def geometry(w):
+    return O.Geometry(w.sx, w.sy, w.nz, w.dx, w.dy, w.zplanes, w.pxl, w.pxr, w.pyl, w.pyr, w.kind,
+                      w.incl_deg, w.decl_deg, w.F_nT)
+
+
+def run(gm, w, prec, m, d):
+    import torch
+
+    op = gm.Operator.from_workload(w, precision=prec)
+    dt = torch.float64 if prec == gm.F64 else torch.float32
+    mt = torch.as_tensor(m, dtype=dt, device="cuda").contiguous()
+    dtn = torch.as_tensor(d, dtype=dt, device="cuda").contiguous()
+    fwd = op.forward(mt)
+    tr = op.transpose(dtn)
+    torch.cuda.synchronize()
+    out = fwd.double().cpu().numpy(), tr.double().cpu().numpy()
+    op.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_grav16_full_vs_oracle(gm, prec):
+    w = W.WORKLOADS["grav16"]
+    geom = geometry(w)
+    m, d = W.model("grav16"), W.data("grav16")
+    fwd, tr = run(gm, w, prec, m, d)
+    assert rel_err(fwd, O.forward(geom, m)) < TOL[prec]
+    assert rel_err(tr, O.transpose(geom, d)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("seed", range(8))
+def test_random_small_shapes_vs_oracle(gm, prec, seed):
+    """Odd, unequal, asymmetric-padded shapes (several tiles and ragged tails in every kernel)."""
+    w = W.random_shape_workload(seed, W.MAGNETIC if seed % 2 else W.GRAVITY)
+    geom = geometry(w)
+    m = W.random_vector(w.model_shape, seed)
+    d = W.random_vector(w.data_shape, seed + 100)
+    fwd, tr = run(gm, w, prec, m, d)
+    assert rel_err(fwd, O.forward(geom, m)) < TOL[prec]
+    assert rel_err(tr, O.transpose(geom, d)) < TOL[prec]
+
+
+EDGE = [
+    W.Workload("one", W.GRAVITY, 1, 1, 1, 10.0, 10.0, 10.0, 0, 0),
+    W.Workload("one_mag", W.MAGNETIC, 1, 1, 1, 10.0, 20.0, 5.0, 0, 0, 45.0, 30.0),
+    W.Workload("row", W.GRAVITY, 13, 1, 3, 10.0, 10.0, 10.0, 4, 0),
+    W.Workload("col", W.MAGNETIC, 1, 17, 2, 10.0, 10.0, 10.0, 0, 5, 60.0, -20.0),
+    W.Workload("pad_heavy", W.MAGNETIC, 3, 2, 2, 10.0, 10.0, 10.0, 9, 11, 30.0, 100.0, 50000.0, 0, 2),
+    W.Workload("primes", W.GRAVITY, 13, 7, 5, 7.0, 11.0, 3.0, 2, 3),
+    W.Workload("pole", W.MAGNETIC, 11, 9, 3, 10.0, 10.0, 10.0, 2, 1, 90.0, 0.0),
+    W.Workload("big_fft", W.GRAVITY, 40, 31, 1, 10.0, 10.0, 10.0, 0, 0),
+]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("w", EDGE, ids=[e.name for e in EDGE])
+def test_edge_shapes_vs_oracle(gm, prec, w):
+    geom = geometry(w)
+    m = W.random_vector(w.model_shape, 5)
+    d = W.random_vector(w.data_shape, 6)
+    fwd, tr = run(gm, w, prec, m, d)
+    assert rel_err(fwd, O.forward(geom, m)) < TOL[prec]
+    assert rel_err(tr, O.transpose(geom, d)) < TOL[prec]
+
+
+def test_variable_layer_depths_vs_oracle(gm):
+    """z_blocks of App. A: layers of different heights, the top one below the stations."""
+    import torch
+
+    z = [2.0, 7.0, 20.0, 22.0, 60.0]
+    geom = O.Geometry(9, 6, 4, 10.0, 15.0, tuple(z), 1, 2, 3, 0, O.MAGNETIC, 55.0, 12.0, 47000.0)
+    for prec, dt in ((gm.F64, torch.float64), (gm.F32, torch.float32)):
+        op = gm.Operator(9, 6, 4, 10.0, 15.0, px=1, pxr=2, py=3, pyr=0, zplanes=z, kind=gm.MAGNETIC,
+                         incl_deg=55.0, decl_deg=12.0, F_nT=47000.0, precision=prec)
+        m = W.random_vector((4, 9, 12), 1)
+        d = W.random_vector((6, 9), 2)
+        f = op.forward(torch.as_tensor(m, dtype=dt, device="cuda")).double().cpu().numpy()
+        t = op.transpose(torch.as_tensor(d, dtype=dt, device="cuda")).double().cpu().numpy()
+        assert rel_err(f, O.forward(geom, m)) < TOL[prec]
+        assert rel_err(t, O.transpose(geom, d)) < TOL[prec]
+
+
+def _golden(name):
+    with open(os.path.join(HERE, "golden", f"sampled_{name}.json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("name", ["mag64", "grav300", "mag128"])
+@pytest.mark.parametrize("prec", [1, 0])
+def test_full_size_sampled_vs_oracle(gm, name, prec):
+    """Full-size workloads, the launch configuration the benchmark uses, against oracle values
+    at sampled stations and cells."""
+    g = _golden(name)
+    w = W.WORKLOADS[name]
+    fwd, tr = run(gm, w, prec, W.model(name, g["model_seed"]), W.data(name, g["data_seed"]))
+    assert rel_err(fwd.ravel()[g["forward_stations"]], g["forward"]) < TOL[prec]
+    assert rel_err(tr.ravel()[g["transpose_cells"]], g["transpose"]) < TOL[prec]
+
+
+@pytest.mark.parametrize("name", ["mag64", "grav300"])
+def test_fp32_whole_vector_vs_fp64(gm, name):
+    """FP32 against the FP64 GPU run over every element (the FP64 run itself is pinned above)."""
+    w = W.WORKLOADS[name]
+    m, d = W.model(name, 0), W.data(name, 0)
+    f64, t64 = run(gm, w, 1, m, d)
+    f32, t32 = run(gm, w, 0, m, d)
+    assert rel_err(f32, f64) < 1e-5
+    assert rel_err(t32, t64) < 1e-5
+
+
+def test_spectrum_is_fft_of_oracle_generator(gm):
+    """The stored spectra equal numpy's 2-D FFT of the circulant generator built from oracle
+    entries (Eqs. Tcircpadded / Tcircpaddedgeneral), so set-up kernels K1-K3 are pinned alone."""
+    w = W.random_shape_workload(3, W.MAGNETIC)
+    geom = geometry(w)
+    op = gm.Operator.from_workload(w, precision=gm.F64)
+    S = op.spectrum()  # [kx][r][ky]
+    Nx, Ny = op.info.fft_nx, op.info.fft_ny
+    T = np.zeros((w.nz, Ny, Nx))
+    for r in range(w.nz):
+        for v in range(-(w.ny - 1), w.sy):
+            j = max(v, 0)
+            for u in range(-(w.nx - 1), w.sx):
+                i = max(u, 0)
+                T[r, v % Ny, u % Nx] = O.entry(geom, i, j, i - u, j - v, r)
+    ref = np.fft.rfft2(T)  # [r][ky][kx]
+    got = np.transpose(S, (1, 2, 0))
+    assert rel_err(got, ref) < 1e-12
+    op.close()
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_dot_product_adjoint(gm, prec):
+    """<G m, d> = <m, G^T d> (Sec. 3: the transpose product uses the same spectra)."""
+    import torch
+
+    w = W.WORKLOADS["mag64"]
+    op = gm.Operator.from_workload(w, precision=prec)
+    dt = op.dtype
+    m = torch.as_tensor(W.random_vector(w.model_shape, 11), dtype=dt, device="cuda")
+    d = torch.as_tensor(W.random_vector(w.data_shape, 12), dtype=dt, device="cuda")
+    a = float((op.forward(m).double() * d.double()).sum())
+    b = float((m.double() * op.transpose(d).double()).sum())
+    scale = float(op.forward(m).double().norm() * d.double().norm())
+    assert abs(a - b) / scale < (1e-14 if prec == 1 else 1e-6)
+    op.close()
+
+
+def test_linearity(gm):
+    import torch
+
+    w = W.WORKLOADS["grav16"]
+    op = gm.Operator.from_workload(w, precision=gm.F64)
+    m1 = torch.as_tensor(W.random_vector(w.model_shape, 1), device="cuda")
+    m2 = torch.as_tensor(W.random_vector(w.model_shape, 2), device="cuda")
+    lhs = op.forward(2.5 * m1 - 0.5 * m2)
+    rhs = 2.5 * op.forward(m1) - 0.5 * op.forward(m2)
+    assert rel_err(lhs.cpu().numpy(), rhs.cpu().numpy()) < 1e-14
+    op.close()
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_host_buffer_entry_points_match_device(gm, prec):
+    import torch
+
+    w = W.WORKLOADS["mag64"]
+    op = gm.Operator.from_workload(w, precision=prec)
+    dt = op.dtype
+    m = torch.as_tensor(W.model("mag64"), dtype=dt).contiguous().pin_memory()
+    d = torch.as_tensor(W.data("mag64"), dtype=dt).contiguous().pin_memory()
+    outd = torch.empty(op.data_shape, dtype=dt).pin_memory()
+    outm = torch.empty(op.model_shape, dtype=dt).pin_memory()
+    op.forward_host(m, outd)
+    op.transpose_host(d, outm)
+    fd = op.forward(m.cuda()).cpu()
+    tm = op.transpose(d.cuda()).cpu()
+    assert torch.equal(outd, fd) and torch.equal(outm, tm)
+    op.close()
+
+
+def test_repeated_applies_are_bitwise_deterministic(gm):
+    import torch
+
+    w = W.WORKLOADS["mag64"]
+    op = gm.Operator.from_workload(w, precision=gm.F32)
+    m = torch.as_tensor(W.model("mag64"), dtype=torch.float32, device="cuda")
+    a = op.forward(m).clone()
+    for _ in range(3):
+        assert torch.equal(op.forward(m), a)
+    op.close()
