@@ -342,7 +342,8 @@ def run_ours(args):
     extra = {}
     if not args.no_fp64:
         op64 = gm.Operator.from_workload(w, precision=gm.F64)
-        m64, d64 = m.double(), d.double()
+        m64 = torch.as_tensor(W.model(w.name, 0), dtype=torch.float64, device="cuda").contiguous()
+        d64 = torch.as_tensor(W.data(w.name, 0), dtype=torch.float64, device="cuda").contiguous()
         od64 = torch.empty(op.data_shape, dtype=torch.float64, device="cuda")
         om64 = torch.empty(op.model_shape, dtype=torch.float64, device="cuda")
         time_steps(op64, m64, d64, od64, om64, flush, 2)
