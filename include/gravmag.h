@@ -169,6 +169,27 @@ GM_API void gm_set_memory_limit(size_t bytes);
 GM_API gm_status gm_cgls(gm_handle h, const void *d_dev, const void *x0_dev, void *x_dev, double alpha,
                   int iters, double *resid_host, void *stream);
 
+/* CGLS exactly like gm_cgls, but without allocating any device memory.  This
+ * entry point has no counterpart in the paper; it exists for callers that
+ * cannot call cudaMalloc when they solve: processes whose GPU memory is
+ * entirely reserved by a framework's pooling allocator, latency-critical loops
+ * that cannot afford the device-wide synchronisation cudaMalloc and cudaFree
+ * may cause, and long-running services that must not grow their device
+ * footprint after start-up.  Its scratch is a fixed 16 MiB array compiled into
+ * the library (gm_cgls_noalloc_capacity() bytes), which every GPU that loads
+ * the library holds until the process exits.  A grid needs
+ * (2 n + 2 m) * element size + 8 * (1032 + iters + 1) bytes, rounded up to 256
+ * for the vectors; larger requests fail with GM_EINVAL and a message, before
+ * anything runs.  The first call on a device looks up the array's device
+ * address (a one-time set-up per device, done with that device current); make
+ * that first call before any stream capture.  All calls in the process share
+ * the array and it keeps the last call's contents (each call clears what it
+ * needs cleared), so calls that overlap on the GPU race: serialise them.
+ * Arguments and results are those of gm_cgls. */
+GM_API gm_status gm_cgls_noalloc(gm_handle h, const void *d_dev, const void *x0_dev, void *x_dev, double alpha,
+                                 int iters, double *resid_host, void *stream);
+GM_API size_t gm_cgls_noalloc_capacity(void);
+
 /* Thread-local status and message of the last failing call of this thread. */
 GM_API gm_status gm_last_status(void);
 GM_API const char *gm_last_error(void);

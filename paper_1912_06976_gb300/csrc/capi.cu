@@ -413,6 +413,26 @@ gm_status gm_cgls(gm_handle h, const void *d_dev, const void *x0_dev, void *x_de
     return ok();
 }
 
+gm_status gm_cgls_noalloc(gm_handle h, const void *d_dev, const void *x0_dev, void *x_dev, double alpha,
+                          int iters, double *resid_host, void *stream) {
+    if (!h) return fail(GM_EINVAL, "handle is NULL");
+    if (!d_dev || !x_dev) return fail(GM_EINVAL, "NULL buffer");
+    if (iters < 0 || !(alpha >= 0) || !std::isfinite(alpha)) return fail(GM_EINVAL, "iters >= 0 and alpha >= 0 required");
+    const size_t need = gm::noalloc_cgls_need(h, iters), cap = gm::noalloc_scratch_bytes();
+    if (need > cap)
+        return fail(GM_EINVAL, "gm_cgls_noalloc needs %zu bytes of scratch for this grid and iteration count; "
+                               "its fixed array holds %zu (use gm_cgls)", need, cap);
+    DeviceGuard dg(h->device);
+    int nl = 0;
+    cudaError_t e = gm::run_cgls_noalloc(h, d_dev, x0_dev, x_dev, alpha, iters, resid_host,
+                                         static_cast<cudaStream_t>(stream), &nl);
+    h->last_launches = nl;
+    if (e != cudaSuccess) return cuda_fail(e, "gm_cgls_noalloc");
+    return ok();
+}
+
+size_t gm_cgls_noalloc_capacity(void) { return gm::noalloc_scratch_bytes(); }
+
 gm_status gm_last_status(void) { return g_last_status; }
 const char *gm_last_error(void) { return g_last_msg; }
 

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <mutex>
 
 #include "gm_plan.h"
 
@@ -208,6 +209,122 @@ out:
 #undef CG_TRY
     *nl = launches;
     return e;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free CGLS (gm_cgls_noalloc).  Same iteration and kernels as cgls_t above, but its
+// scratch (four vectors, the reduction partials, the scalars and the residual history) lives in
+// one fixed file-scope device array instead of memory the handle allocates on first use.  The
+// array is shared by every call in the process: its contents persist between calls and calls
+// that overlap on the GPU would race on it.
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB on every GPU that loads the library
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mutex;
+static void *g_noalloc_ptr[kMaxDevices] = {};
+
+size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
+
+// Device address of the array on the current device, looked up once per device (the host-side
+// name of a __device__ variable is not a device address).
+static cudaError_t noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+size_t noalloc_cgls_need(const gm_plan *p, int iters) {
+    const size_t n = (size_t)p->geo.nx * p->geo.ny * p->geo.nz, m = (size_t)p->geo.sx * p->geo.sy;
+    const size_t el = p->precision == GM_F64 ? sizeof(double) : sizeof(float);
+    return ((el * (2 * n + 2 * m) + 255) / 256) * 256 + sizeof(double) * (2 * kRedBlocks + S_COUNT + (size_t)iters + 1);
+}
+
+template <typename R>
+static cudaError_t cgls_noalloc_t(gm_plan *p, const R *d, const R *x0, R *x, double alpha, int iters,
+                                  double *resid_host, cudaStream_t st, int *nl) {
+    const size_t n = (size_t)p->geo.nx * p->geo.ny * p->geo.nz, m = (size_t)p->geo.sx * p->geo.sy;
+    void *scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) return e;
+    char *base = static_cast<char *>(scratch);
+    R *s = reinterpret_cast<R *>(base);
+    R *pv = s + n;
+    R *r = pv + n;
+    R *q = r + m;
+    double *part = reinterpret_cast<double *>(base + ((sizeof(R) * (2 * n + 2 * m) + 255) / 256) * 256);
+    double *sc = part + 2 * kRedBlocks;
+    double *resid = sc + S_COUNT;
+    int launches = 0, k = 0;
+    const int vb = kRedBlocks, vt = kRedThreads;
+#define NA_TRY(x)                                  \
+    do {                                           \
+        e = (x);                                   \
+        if (e != cudaSuccess) goto out;            \
+    } while (0)
+    // the array keeps the previous call's values: start the scalars and history from zero
+    NA_TRY(cudaMemsetAsync(sc, 0, sizeof(double) * (S_COUNT + (size_t)iters + 1), st));
+    if (x0 && x0 != x) NA_TRY(cudaMemcpyAsync(x, x0, sizeof(R) * n, cudaMemcpyDeviceToDevice, st));
+    if (!x0) NA_TRY(cudaMemsetAsync(x, 0, sizeof(R) * n, st));
+    {
+        int l = 0;
+        NA_TRY(launch_forward(p, x, r, st, &l));
+        launches += l;
+    }
+    k_residual0<R><<<vb, vt, 0, st>>>(d, r, m);
+    {
+        int l = 0;
+        NA_TRY(launch_transpose(p, r, s, st, &l));
+        launches += l;
+    }
+    k_s_update<R><<<vb, vt, 0, st>>>(s, x, pv, n, (R)(alpha * alpha), 1);
+    k_sumsq2<R><<<vb, vt, 0, st>>>(s, n, r, m, part);
+    k_init_scalars<<<1, 1024, 0, st>>>(part, sc, resid, alpha * alpha);
+    launches += 4;
+    for (k = 1; k <= iters; ++k) {
+        int l = 0;
+        NA_TRY(launch_forward(p, pv, q, st, &l));
+        launches += l;
+        k_sumsq2<R><<<vb, vt, 0, st>>>(q, m, pv, n, part);
+        k_step_length<<<1, 1024, 0, st>>>(part, sc);
+        k_update_xr<R><<<vb, vt, 0, st>>>(x, pv, n, r, q, m, sc);
+        NA_TRY(launch_transpose(p, r, s, st, &l));
+        launches += l;
+        k_s_update<R><<<vb, vt, 0, st>>>(s, x, pv, n, (R)(alpha * alpha), 0);
+        k_sumsq2<R><<<vb, vt, 0, st>>>(s, n, r, m, part);
+        k_beta<<<1, 1024, 0, st>>>(part, sc, resid, k);
+        k_update_p<R><<<vb, vt, 0, st>>>(pv, s, n, sc);
+        launches += 6;
+        NA_TRY(cudaGetLastError());
+    }
+    NA_TRY(cudaGetLastError());
+    if (resid_host) {
+        NA_TRY(cudaMemcpyAsync(resid_host, resid, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost, st));
+        NA_TRY(cudaStreamSynchronize(st));
+    }
+out:
+#undef NA_TRY
+    *nl = launches;
+    return e;
+}
+
+cudaError_t run_cgls_noalloc(gm_plan *p, const void *d, const void *x0, void *x, double alpha, int iters,
+                             double *resid_host, cudaStream_t s, int *nl) {
+    if (p->precision == GM_F64)
+        return cgls_noalloc_t<double>(p, static_cast<const double *>(d), static_cast<const double *>(x0),
+                                      static_cast<double *>(x), alpha, iters, resid_host, s, nl);
+    return cgls_noalloc_t<float>(p, static_cast<const float *>(d), static_cast<const float *>(x0),
+                                 static_cast<float *>(x), alpha, iters, resid_host, s, nl);
 }
 
 cudaError_t run_cgls(gm_plan *p, const void *d, const void *x0, void *x, double alpha, int iters, double *resid_host,

@@ -89,4 +89,10 @@ cudaError_t launch_transpose(gm_plan *p, const void *d, void *m, cudaStream_t s,
 cudaError_t run_cgls(gm_plan *p, const void *d, const void *x0, void *x, double alpha, int iters,
                      double *resid_host, cudaStream_t s, int *nl);
 
+// Allocation-free CGLS on the fixed scratch array of cgls.cu; its capacity and the bytes a plan needs.
+cudaError_t run_cgls_noalloc(gm_plan *p, const void *d, const void *x0, void *x, double alpha, int iters,
+                             double *resid_host, cudaStream_t s, int *nl);
+size_t noalloc_scratch_bytes();
+size_t noalloc_cgls_need(const gm_plan *p, int iters);
+
 }  // namespace gm

@@ -108,6 +108,8 @@ def load():
             "gm_status_string": (ctypes.c_char_p, [c_int]),
             "gm_last_launch_count": (c_int, [vp]),
             "gm_enable_timing": (c_int, [vp, c_int]),
+            "gm_cgls_noalloc": (c_int, [vp, vp, vp, vp, c_double, c_int, ctypes.POINTER(c_double), vp]),
+            "gm_cgls_noalloc_capacity": (c_size_t, []),
             "gm_kernel_times": (c_int, [vp, ctypes.POINTER(KernelTime), c_int]),
         }
         for name, (res, args) in sig.items():
@@ -279,6 +281,16 @@ class Operator:
         x0p = self._arg(x0, self.info.n_model) if x0 is not None else ctypes.c_void_p(0)
         _check(load().gm_cgls(self._h, self._arg(d, self.info.n_data), x0p, self._arg(out, self.info.n_model),
                               float(alpha), int(iters), res, _stream_ptr(stream)))
+        return out, (np.array(res[:]) if residuals else None)
+
+    def cgls_noalloc(self, d, alpha, iters, out, x0=None, stream=None, residuals=True):
+        """Like cgls(), through the entry point that allocates no device memory (its scratch is a
+        fixed array inside the library); the caller passes the output tensor."""
+        res = (ctypes.c_double * (iters + 1))() if residuals else None
+        x0p = self._arg(x0, self.info.n_model) if x0 is not None else ctypes.c_void_p(0)
+        _check(load().gm_cgls_noalloc(self._h, self._arg(d, self.info.n_data), x0p,
+                                      self._arg(out, self.info.n_model), float(alpha), int(iters), res,
+                                      _stream_ptr(stream)))
         return out, (np.array(res[:]) if residuals else None)
 
     def last_launch_count(self) -> int:
