@@ -126,12 +126,14 @@ static cudaError_t transpose_t(gm_plan *p, const R *d, R *m, cudaStream_t s, int
 }
 
 cudaError_t launch_forward(gm_plan *p, const void *m, void *d, cudaStream_t s, int *nl) {
+    if (p->fast) return launch_forward_fast(p, m, d, s, nl);
     if (p->precision == GM_F64)
         return forward_t<double>(p, static_cast<const double *>(m), static_cast<double *>(d), s, nl);
     return forward_t<float>(p, static_cast<const float *>(m), static_cast<float *>(d), s, nl);
 }
 
 cudaError_t launch_transpose(gm_plan *p, const void *d, void *m, cudaStream_t s, int *nl) {
+    if (p->fast) return launch_transpose_fast(p, d, m, s, nl);
     if (p->precision == GM_F64)
         return transpose_t<double>(p, static_cast<const double *>(d), static_cast<double *>(m), s, nl);
     return transpose_t<float>(p, static_cast<const float *>(d), static_cast<float *>(m), s, nl);

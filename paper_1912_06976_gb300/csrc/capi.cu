@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -60,12 +61,18 @@ constexpr double kPi = 3.14159265358979323846264338327950288;
 constexpr double kGamma = 6.67430e-3;  // mGal per (g/cm^3 m)
 constexpr int kMaxFft = 4800;          // one FFT column / row must fit a CTA's shared memory in FP64
 
+// GM_GENERIC_FFT=1 in the environment selects the generic kernels for every length.
+bool fast_disabled() {
+    const char *v = std::getenv("GM_GENERIC_FFT");
+    return v && v[0] == '1';
+}
+
 }  // namespace
 
 namespace gm {
 
 const char *const kKernelNames[K_COUNT] = {"fwd_rows_r2c", "fwd_cols_mac", "fwd_rows_c2r", "tr_rows_r2c",
-                                           "tr_cols",      "tr_rows_c2r",  "cgls_vec"};
+                                           "tr_cols",      "tr_rows_c2r",  "cgls_vec",     "fwd_cols_inv"};
 
 bool make_radices(int N, FftDesc &d) {
     d.N = N;
@@ -118,6 +125,7 @@ static void free_plan(gm_plan *p) {
     cudaFree(p->spec);
     cudaFree(p->work_big);
     cudaFree(p->work_small);
+    cudaFree(p->work_part);
     cudaFree(p->stage_m);
     cudaFree(p->stage_d);
     cudaFree(p->tw_x);
@@ -228,7 +236,13 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
     const size_t big = cel * (size_t)g.Kx * g.nz * g.ny;
     const size_t small = cel * (size_t)g.Kx * g.sy;
     const size_t n_model = (size_t)g.nx * g.ny * g.nz, n_data = (size_t)g.sx * g.sy;
-    p->work_bytes = big + small + rel * (n_model + n_data);
+    p->fast = !fast_disabled() && gm::fast_path_supported(g.NPx, g.NPy);
+    size_t part = 0;
+    if (p->fast) {
+        gm::fast_plan_groups(p);
+        part = cel * (size_t)p->fast_groups_fwd * g.Kx * g.NPy;
+    }
+    p->work_bytes = big + small + part + rel * (n_model + n_data);
     const size_t setup_peak = sizeof(double) * ((size_t)(p->Nx + 1) * (p->Ny + 1) * g.nz +
                                                 (size_t)g.NPx * g.NPy * g.nz) +
                               sizeof(double2) * nspec + 4 * sizeof(double2) * (g.NPx + g.NPy);
@@ -262,6 +276,7 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
     SETUP_TRY(cudaMalloc(&p->spec, p->spec_bytes), "spectra");
     SETUP_TRY(cudaMalloc(&p->work_big, big), "workspace");
     SETUP_TRY(cudaMalloc(&p->work_small, small), "workspace");
+    if (part) SETUP_TRY(cudaMalloc(&p->work_part, part), "workspace");
     SETUP_TRY(cudaMalloc(&p->stage_m, rel * n_model), "staging");
     SETUP_TRY(cudaMalloc(&p->stage_d, rel * n_data), "staging");
     cudaStream_t s;

@@ -13,6 +13,11 @@
 //   repeat: q = G p;  delta = ||q||^2 + alpha^2 ||p||^2;  a = gamma / delta
 //           x += a p;  r -= a q;  s = G^T r - alpha^2 x
 //           gamma' = ||s||^2;  b = gamma' / gamma;  gamma = gamma';  p = s + b p
+//
+// Once ||s|| has fallen to rounding level (||s|| <= 64 eps ||s_0||, eps of the vector
+// precision) the iterate is the regularised solution to working accuracy; further steps would
+// only act on rounding noise (the FFT transpose is G^T to rounding, not exactly), so the
+// remaining iterations keep x and r unchanged.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -26,7 +31,7 @@ constexpr int kRedBlocks = 512;
 constexpr int kRedThreads = 256;
 
 // scalar slots
-enum { S_GAMMA = 0, S_A = 1, S_B = 2, S_ALPHA2 = 3, S_COUNT = 8 };
+enum { S_GAMMA = 0, S_A = 1, S_B = 2, S_ALPHA2 = 3, S_THRESH = 4, S_DONE = 5, S_COUNT = 8 };
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -63,40 +68,50 @@ __device__ double sum_parts(const double *part, double *sh) {
     return block_sum(v, sh);
 }
 
-// init: gamma = ||s||^2 (parts[0..]); resid[0] = sqrt(||r||^2) (parts[K..])
-__global__ void k_init_scalars(const double *part, double *sc, double *resid, double alpha2) {
+// init: gamma = ||s||^2 (parts[0..]); resid[0] = sqrt(||r||^2) (parts[K..]);
+// converged once gamma <= tol2 * gamma_0
+__global__ void k_init_scalars(const double *part, double *sc, double *resid, double alpha2, double tol2) {
     __shared__ double sh[32];
     double s2 = sum_parts(part, sh);
     double r2 = sum_parts(part + kRedBlocks, sh);
     if (threadIdx.x == 0) {
         sc[S_GAMMA] = s2;
         sc[S_ALPHA2] = alpha2;
+        sc[S_THRESH] = tol2 * s2;
+        sc[S_DONE] = (s2 > 0) ? 0.0 : 1.0;
         resid[0] = sqrt(r2);
     }
 }
 
-// a = gamma / (||q||^2 + alpha^2 ||p||^2)
+// a = gamma / (||q||^2 + alpha^2 ||p||^2), or 0 once converged
 __global__ void k_step_length(const double *part, double *sc) {
     __shared__ double sh[32];
     double q2 = sum_parts(part, sh);
     double p2 = sum_parts(part + kRedBlocks, sh);
     if (threadIdx.x == 0) {
+        if (sc[S_GAMMA] <= sc[S_THRESH]) sc[S_DONE] = 1.0;
         double delta = q2 + sc[S_ALPHA2] * p2;
-        sc[S_A] = (delta > 0) ? sc[S_GAMMA] / delta : 0.0;
+        sc[S_A] = (sc[S_DONE] == 0.0 && delta > 0) ? sc[S_GAMMA] / delta : 0.0;
     }
 }
 
-// b = gamma' / gamma, gamma = gamma'; resid[k] = ||r||
+// b = gamma' / gamma (0 once converged), gamma = gamma'; resid[k] = ||r||
 __global__ void k_beta(const double *part, double *sc, double *resid, int k) {
     __shared__ double sh[32];
     double s2 = sum_parts(part, sh);
     double r2 = sum_parts(part + kRedBlocks, sh);
     if (threadIdx.x == 0) {
         double g = sc[S_GAMMA];
-        sc[S_B] = (g > 0) ? s2 / g : 0.0;
+        sc[S_B] = (sc[S_DONE] == 0.0 && g > 0) ? s2 / g : 0.0;
         sc[S_GAMMA] = s2;
         resid[k] = sqrt(r2);
     }
+}
+
+// Convergence threshold on ||s||^2 / ||s_0||^2 for vectors of type R.
+template <typename R> constexpr double cgls_tol2() {
+    return (64.0 * (sizeof(R) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07)) *
+           (64.0 * (sizeof(R) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07));
 }
 
 // r = d - r (r holds G x0 on entry)
@@ -182,7 +197,7 @@ static cudaError_t cgls_t(gm_plan *p, const R *d, const R *x0, R *x, double alph
     }
     k_s_update<R><<<vb, vt, 0, st>>>(s, x, pv, n, (R)(alpha * alpha), 1);
     k_sumsq2<R><<<vb, vt, 0, st>>>(s, n, r, m, part);
-    k_init_scalars<<<1, 1024, 0, st>>>(part, sc, resid, alpha * alpha);
+    k_init_scalars<<<1, 1024, 0, st>>>(part, sc, resid, alpha * alpha, cgls_tol2<R>());
     launches += 4;
     for (k = 1; k <= iters; ++k) {
         int l = 0;
@@ -289,7 +304,7 @@ static cudaError_t cgls_noalloc_t(gm_plan *p, const R *d, const R *x0, R *x, dou
     }
     k_s_update<R><<<vb, vt, 0, st>>>(s, x, pv, n, (R)(alpha * alpha), 1);
     k_sumsq2<R><<<vb, vt, 0, st>>>(s, n, r, m, part);
-    k_init_scalars<<<1, 1024, 0, st>>>(part, sc, resid, alpha * alpha);
+    k_init_scalars<<<1, 1024, 0, st>>>(part, sc, resid, alpha * alpha, cgls_tol2<R>());
     launches += 4;
     for (k = 1; k <= iters; ++k) {
         int l = 0;

@@ -1,0 +1,201 @@
+"""Generates gm_fft_codelets.cuh: straight-line small DFTs for the register-resident FFT passes.
+
+Each codelet dft<N>(v) transforms v[0..N-1] in place, natural order in and out,
+forward (X_k = SUM_n x_n exp(-2 pi i n k / N)) or inverse (+i, unnormalised).
+Odd primes use the symmetric-pair form (N-1)/2 real cosines and sines; 4 uses
+the radix-4 butterfly; composite sizes are split N = N1 * N2 (Cooley-Tukey,
+input n = N2 n1 + n2, output k = k1 + N1 k2) with the twiddles exp(-2 pi i
+n2 k1 / N) emitted as literals; multiplications by +-1, +-i and (+-1 +- i)/sqrt2
+are specialised.  Constants are computed here in double precision with Python's
+math module and written with 17 significant digits.
+
+Run:  python gen_fft_codelets.py   (self-tests every codelet against numpy's FFT by executing
+the emitted statements in Python, then rewrites gm_fft_codelets.cuh next to this file)
+"""
+import math
+import os
+import re
+
+import mpmath
+
+mpmath.mp.dps = 40
+
+
+def cos2pi(k, n):
+    return float(mpmath.cos(2 * mpmath.pi * k / n))
+
+
+def sin2pi(k, n):
+    return float(mpmath.sin(2 * mpmath.pi * k / n))
+
+SIZES = [2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 20, 21, 24, 25, 27, 28, 32, 35]
+
+# preferred split of composite sizes (N1, N2)
+SPLITS = {6: (2, 3), 8: (2, 4), 9: (3, 3), 10: (2, 5), 12: (4, 3), 14: (2, 7), 15: (3, 5), 16: (4, 4),
+          20: (4, 5), 21: (3, 7), 24: (8, 3), 25: (5, 5), 27: (3, 9), 28: (4, 7), 32: (4, 8), 35: (5, 7)}
+
+
+def lit(x):
+    if x == 0.0:
+        return "R(0)"
+    return f"R({x:.17g})"
+
+
+class Emitter:
+    def __init__(self):
+        self.lines = []
+        self.n = 0
+
+    def tmp(self):
+        self.n += 1
+        return f"t{self.n}"
+
+    def let(self, expr):
+        t = self.tmp()
+        self.lines.append(f"const R {t} = {expr};")
+        return t
+
+    # complex values are (re, im) pairs of expression names
+    def add(self, a, b):
+        return (self.let(f"{a[0]} + {b[0]}"), self.let(f"{a[1]} + {b[1]}"))
+
+    def sub(self, a, b):
+        return (self.let(f"{a[0]} - {b[0]}"), self.let(f"{a[1]} - {b[1]}"))
+
+    def mul_i(self, a, sign):
+        """a * (sign * i)"""
+        return (self.let(f"-{a[1]}") if sign > 0 else a[1], a[0] if sign > 0 else self.let(f"-{a[0]}"))
+
+    def twiddle(self, a, k, n, sign):
+        """a * exp(sign * 2 pi i k / n)"""
+        k %= n
+        if k == 0:
+            return a
+        if 4 * k == n:
+            return self.mul_i(a, sign)
+        if 2 * k == n:
+            return (self.let(f"-{a[0]}"), self.let(f"-{a[1]}"))
+        if 4 * k == 3 * n:
+            return self.mul_i(a, -sign)
+        c = cos2pi(k, n)
+        s = sign * sin2pi(k, n)
+        if 8 * k % n == 0:  # odd multiples of pi/4: (c, s) = (+-h, +-h)
+            h = lit(abs(c))
+            # (x + i y)(c + i s) = (x c - y s) + i (x s + y c) with |c| = |s| = h
+            sc, ss = (1 if c > 0 else -1), (1 if s > 0 else -1)
+            re = self.let(f"({a[0]} {'-' if ss * sc > 0 else '+'} {a[1]}) * {lit(c)}")
+            im = self.let(f"({a[0]} {'+' if ss * sc > 0 else '-'} {a[1]}) * {lit(s)}")
+            del h
+            return (re, im)
+        return (self.let(f"{a[0]} * {lit(c)} - {a[1]} * {lit(s)}"),
+                self.let(f"{a[0]} * {lit(s)} + {a[1]} * {lit(c)}"))
+
+    def dft(self, x, sign):
+        n = len(x)
+        if n == 1:
+            return list(x)
+        if n == 2:
+            return [self.add(x[0], x[1]), self.sub(x[0], x[1])]
+        if n == 4:
+            t0, t1 = self.add(x[0], x[2]), self.sub(x[0], x[2])
+            t2, t3 = self.add(x[1], x[3]), self.sub(x[1], x[3])
+            it3 = self.mul_i(t3, sign)
+            return [self.add(t0, t2), self.add(t1, it3), self.sub(t0, t2), self.sub(t1, it3)]
+        if n in SPLITS:
+            n1, n2 = SPLITS[n]
+            y = [[None] * n1 for _ in range(n2)]
+            for b in range(n2):
+                col = self.dft([x[n2 * a + b] for a in range(n1)], sign)
+                for k1 in range(n1):
+                    y[b][k1] = self.twiddle(col[k1], b * k1, n, sign)
+            out = [None] * n
+            for k1 in range(n1):
+                row = self.dft([y[b][k1] for b in range(n2)], sign)
+                for k2 in range(n2):
+                    out[k1 + n1 * k2] = row[k2]
+            return out
+        # odd prime: symmetric pairs
+        assert n % 2 == 1
+        h = (n - 1) // 2
+        a = [self.add(x[k], x[n - k]) for k in range(1, h + 1)]
+        b = [self.sub(x[k], x[n - k]) for k in range(1, h + 1)]
+        s0r = " + ".join([x[0][0]] + [ak[0] for ak in a])
+        s0i = " + ".join([x[0][1]] + [ak[1] for ak in a])
+        out = [None] * n
+        out[0] = (self.let(s0r), self.let(s0i))
+        for m in range(1, h + 1):
+            cs = [cos2pi(k * m, n) for k in range(1, h + 1)]
+            ss = [sin2pi(k * m, n) for k in range(1, h + 1)]
+            Ar = self.let(" + ".join([x[0][0]] + [f"{a[k][0]} * {lit(cs[k])}" for k in range(h)]))
+            Ai = self.let(" + ".join([x[0][1]] + [f"{a[k][1]} * {lit(cs[k])}" for k in range(h)]))
+            Br = self.let(" + ".join([f"{b[k][0]} * {lit(ss[k])}" for k in range(h)]))
+            Bi = self.let(" + ".join([f"{b[k][1]} * {lit(ss[k])}" for k in range(h)]))
+            # X_m = A + sign*i*B, X_{n-m} = A - sign*i*B
+            if sign < 0:
+                out[m] = (self.let(f"{Ar} + {Bi}"), self.let(f"{Ai} - {Br}"))
+                out[n - m] = (self.let(f"{Ar} - {Bi}"), self.let(f"{Ai} + {Br}"))
+            else:
+                out[m] = (self.let(f"{Ar} - {Bi}"), self.let(f"{Ai} + {Br}"))
+                out[n - m] = (self.let(f"{Ar} + {Bi}"), self.let(f"{Ai} - {Br}"))
+        return out
+
+
+def codelet(n, inverse):
+    e = Emitter()
+    x = [(f"v[{k}].x", f"v[{k}].y") for k in range(n)]
+    out = e.dft(x, +1 if inverse else -1)
+    body = ["    " + ln for ln in e.lines]
+    body += [f"    v[{k}].x = {out[k][0]};" for k in range(n)]
+    body += [f"    v[{k}].y = {out[k][1]};" for k in range(n)]
+    name = "idft" if inverse else "dft"
+    return (f"template <typename C>\n__device__ __forceinline__ void {name}{n}(C (&v)[{n}]) {{\n"
+            f"    using R = decltype(v[0].x);\n" + "\n".join(body) + "\n}\n")
+
+
+def selftest():
+    """Executes every emitted codelet body in Python and compares it with numpy's FFT."""
+    import numpy as np
+
+    rng = np.random.default_rng(0)
+    worst = 0.0
+    for n in SIZES:
+        for inv in (False, True):
+            e = Emitter()
+            out = e.dft([(f"vx[{k}]", f"vy[{k}]") for k in range(n)], +1 if inv else -1)
+            code = [re.sub(r"R\(([^)]*)\)", r"\1", ln.replace("const R ", "")).rstrip(";") for ln in e.lines]
+            x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+            env = {"vx": list(x.real), "vy": list(x.imag)}
+            exec("\n".join(code), env)
+            got = np.array([eval(o[0], env) + 1j * eval(o[1], env) for o in out])
+            ref = np.fft.ifft(x) * n if inv else np.fft.fft(x)
+            err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+            worst = max(worst, err)
+            assert err < 1e-14, (n, inv, err)
+    return worst
+
+
+def main():
+    parts = ["// gm_fft_codelets.cuh -- GENERATED by gen_fft_codelets.py; do not edit by hand.",
+             "// Straight-line in-register DFTs, natural order: dftN (forward, exp(-2 pi i nk/N)) and",
+             "// idftN (inverse, exp(+2 pi i nk/N), unnormalised), for C = float2 or double2.",
+             "#pragma once", "", "namespace gm {", "namespace cl {", ""]
+    for n in SIZES:
+        parts.append(codelet(n, False))
+        parts.append(codelet(n, True))
+    parts.append("// Dispatch by size: Dft<N, INV>::run(v).")
+    parts.append("template <int N, bool INV> struct Dft;")
+    for n in SIZES:
+        for inv in (False, True):
+            nm = ("idft" if inv else "dft") + str(n)
+            parts.append(f"template <> struct Dft<{n}, {'true' if inv else 'false'}> {{ template <typename C> "
+                         f"__device__ __forceinline__ static void run(C (&v)[{n}]) {{ {nm}(v); }} }};")
+    parts += ["", "}  // namespace cl", "}  // namespace gm", ""]
+    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "gm_fft_codelets.cuh")
+    with open(out, "w") as f:
+        f.write("\n".join(parts))
+    print(out)
+
+
+if __name__ == "__main__":
+    print("self-test: worst relative error", selftest())
+    main()

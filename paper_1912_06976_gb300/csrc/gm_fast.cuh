@@ -1,0 +1,384 @@
+// gm_fast.cuh -- register-resident two-pass FFT kernels of the apply path.
+//
+// A transform of length N = R1 * R2 runs as two passes of straight-line DFT
+// codelets in registers with one shared-memory exchange between them
+// (Stockham order, natural order in and out):
+//   pass 1: item j < R2 takes x[j + R2*rr] (rr < R1), runs DFT-R1 and stores its
+//           outputs s < R1 in exchange row j (index n = R1*j + s);
+//   pass 2: item j < R1 takes y[j + R1*rr] (rr < R2), multiplies by the twiddle
+//           exp(-+2 pi i rr j / N), runs DFT-R2 and holds X[j + R1*s] (s < R2).
+// Exchange rows are padded to an odd pitch so that both the row-wise stores of
+// pass 1 and the column-wise loads of pass 2 hit distinct shared-memory banks.
+//
+// The kernels realise the steps of Eq. GrviaT / Algorithm multbttb (see apply.cu
+// for the data flow); each keeps its inputs and outputs coalesced by choosing which
+// of the two radices faces global memory.
+#pragma once
+
+#include "gm_common.cuh"
+#include "gm_fft_codelets.cuh"
+
+namespace gm {
+namespace fast {
+
+template <int R> struct Pitch { static constexpr int value = (R % 2) ? R : R + 1; };
+
+// Exchange size (complex values) of one transform whose pass 1 has radix R1.
+template <int R1, int R2> struct Ex { static constexpr int value = R2 * Pitch<R1>::value; };
+
+template <int R1, bool INV, typename C>
+__device__ __forceinline__ void pass1_store(C (&v)[R1], C *ex, int j) {
+    cl::Dft<R1, INV>::run(v);
+    constexpr int P = Pitch<R1>::value;
+#pragma unroll
+    for (int s = 0; s < R1; ++s) ex[j * P + s] = v[s];
+}
+
+template <int R1, int R2, typename C>
+__device__ __forceinline__ void pass2_gather(C (&v)[R2], const C *ex, int j) {
+    constexpr int P = Pitch<R1>::value;
+#pragma unroll
+    for (int rr = 0; rr < R2; ++rr) v[rr] = ex[rr * P + j];
+}
+
+// twiddles from a table of exp(-2 pi i e / N), e < N (conjugated for the inverse)
+template <int R1, int R2, bool INV, typename C>
+__device__ __forceinline__ void pass2_twiddle_table(C (&v)[R2], const C *tw, int j) {
+#pragma unroll
+    for (int rr = 1; rr < R2; ++rr) {
+        C w = tw[rr * j];
+        if (INV) w.y = -w.y;
+        v[rr] = c_mul(v[rr], w);
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ void load_table(C *dst, const C *src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// ------------------------------------------------------------------------------------------
+// Real rows -> half spectra (two rows per complex transform, N = R1*R2 = N'_x).
+// Block (pair group, layer) transforms rows q0 .. q0 + 2*PAIRS - 1 of `layer` of
+// in[layer][row][0:row_len] and writes out[k][layer][row] (row stride out_rows), k < N/2+1.
+template <typename C, typename Rin, int R1, int R2, int PAIRS>
+__global__ void __launch_bounds__(256) k_rows_r2c(const Rin *__restrict__ in, int rows, int row_len, int nlayers,
+                                                  C *__restrict__ out, int out_rows, const C *__restrict__ twg) {
+    constexpr int N = R1 * R2, EX = Ex<R1, R2>::value, Kx = N / 2 + 1;
+    extern __shared__ unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *ex = tw + N;
+    const int q0 = blockIdx.x * 2 * PAIRS;
+    const int layer = blockIdx.y;
+    load_table(tw, twg, N);
+    for (int it = threadIdx.x; it < PAIRS * R2; it += blockDim.x) {
+        const int p = it / R2, j = it - p * R2;
+        const int qa = q0 + 2 * p;
+        const bool va = qa < rows, vb = qa + 1 < rows;
+        const Rin *ra = in + ((size_t)layer * rows + qa) * row_len;
+        C v[R1];
+#pragma unroll
+        for (int rr = 0; rr < R1; ++rr) {
+            const int n = j + R2 * rr;
+            const bool ok = n < row_len;
+            v[rr].x = (ok && va) ? (decltype(v[0].x))ra[n] : 0;
+            v[rr].y = (ok && vb) ? (decltype(v[0].x))ra[row_len + n] : 0;
+        }
+        pass1_store<R1, false>(v, ex + p * EX, j);
+    }
+    __syncthreads();
+    // pass 2 keeps its outputs in registers until every thread has read the exchange
+    C v[R2];
+    const int it2 = threadIdx.x;
+    const bool act = it2 < PAIRS * R1;
+    const int p2 = act ? it2 / R1 : 0, j2 = act ? it2 - p2 * R1 : 0;
+    if (act) {
+        pass2_gather<R1, R2>(v, ex + p2 * EX, j2);
+        pass2_twiddle_table<R1, R2, false>(v, tw, j2);
+        cl::Dft<R2, false>::run(v);
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int s = 0; s < R2; ++s) ex[p2 * EX + j2 + R1 * s] = v[s];  // natural order Z[k]
+    }
+    __syncthreads();
+    // separate the two real rows: FFT(a)[k] = (Z[k] + conj Z[-k]) / 2, FFT(b)[k] = (Z[k] - conj Z[-k]) / 2i
+    for (int it = threadIdx.x; it < PAIRS * Kx; it += blockDim.x) {
+        const int k = it / PAIRS, p = it - k * PAIRS;
+        const int qa = q0 + 2 * p;
+        if (qa >= rows) continue;
+        const C a = ex[p * EX + k];
+        const C b = c_conj(ex[p * EX + (k == 0 ? 0 : N - k)]);
+        C x1, x2;
+        x1.x = (a.x + b.x) * 0.5f;
+        x1.y = (a.y + b.y) * 0.5f;
+        x2.x = (a.y - b.y) * 0.5f;
+        x2.y = (b.x - a.x) * 0.5f;
+        C *o = out + ((size_t)k * nlayers + layer) * out_rows + qa;
+        o[0] = x1;
+        if (qa + 1 < rows) o[1] = x2;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Half spectra -> real rows (two rows per complex inverse transform, N = R1*R2 = N'_x).
+// X(k, layer, row) = in[k*ld_k + layer*ld_layer + row*ld_row], k < N/2+1; writes
+// out[layer][row][0:row_len_out] = scale * (inverse transform)[0:row_len_out].
+template <typename C, typename Rout, int R1, int R2, int PAIRS>
+__global__ void __launch_bounds__(256) k_rows_c2r(const C *__restrict__ in, long long ld_k, long long ld_layer,
+                                                  long long ld_row, int rows, Rout *__restrict__ out, int row_len_out,
+                                                  double scale, const C *__restrict__ twg) {
+    constexpr int N = R1 * R2, EX = Ex<R1, R2>::value, Kx = N / 2 + 1, H = N / 2;
+    extern __shared__ unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *xs = tw + N;                 // [2*PAIRS][Kx]
+    C *ex = xs + 2 * PAIRS * Kx;    // [PAIRS][EX]
+    const int q0 = blockIdx.x * 2 * PAIRS;
+    const int layer = blockIdx.y;
+    load_table(tw, twg, N);
+    for (int it = threadIdx.x; it < Kx * 2 * PAIRS; it += blockDim.x) {
+        const int k = it / (2 * PAIRS), row = it - k * 2 * PAIRS;
+        const int q = q0 + row;
+        xs[row * Kx + k] = (q < rows) ? in[k * ld_k + layer * ld_layer + q * ld_row] : c_make<C>(0, 0);
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < PAIRS * R2; it += blockDim.x) {
+        const int p = it / R2, j = it - p * R2;
+        const C *x1r = xs + (2 * p) * Kx, *x2r = x1r + Kx;
+        C v[R1];
+#pragma unroll
+        for (int rr = 0; rr < R1; ++rr) {
+            const int n = j + R2 * rr;
+            const int kk = (n <= H) ? n : N - n;
+            C a = x1r[kk], b = x2r[kk];
+            if (n > H) { a.y = -a.y; b.y = -b.y; }
+            v[rr] = c_make<C>(a.x - b.y, a.y + b.x);  // X1 + i X2
+        }
+        pass1_store<R1, true>(v, ex + p * EX, j);
+    }
+    __syncthreads();
+    const auto sc = (decltype(tw[0].x))scale;
+    for (int it = threadIdx.x; it < PAIRS * R1; it += blockDim.x) {
+        const int p = it / R1, j = it - p * R1;
+        C v[R2];
+        pass2_gather<R1, R2>(v, ex + p * EX, j);
+        pass2_twiddle_table<R1, R2, true>(v, tw, j);
+        cl::Dft<R2, true>::run(v);
+        const int qa = q0 + 2 * p;
+        Rout *oa = out + ((size_t)layer * rows + qa) * row_len_out;
+#pragma unroll
+        for (int s = 0; s < R2; ++s) {
+            const int i = j + R1 * s;
+            if (i < row_len_out) {
+                if (qa < rows) oa[i] = (Rout)(v[s].x * sc);
+                if (qa + 1 < rows) oa[row_len_out + i] = (Rout)(v[s].y * sc);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Forward column pass with the depth multiply-accumulate (N = R1*R2 = N'_y).
+// Block (column group, layer group): for its COLS columns kx and layers r in the group,
+// acc[kx][k] = SUM_r S[kx][r][k] * FFT_y(A[kx][r][0:ny])[k]; writes acc to part[group][kx][k].
+// Pass-2 thread (c, j) owns k = j + R1*s (s < R2) for every layer, so acc stays in registers.
+template <typename C, int R1, int R2, int COLS, int LSTEP>
+__global__ void __launch_bounds__(COLS * R1 <= 256 ? 256 : 512)
+    k_cols_fwd_mac(const C *__restrict__ A, const C *__restrict__ S, C *__restrict__ part, int Kx, int nz, int ny,
+                   int layers_per_group, const C *__restrict__ twg) {
+    constexpr int N = R1 * R2, EX = Ex<R1, R2>::value;
+    extern __shared__ unsigned char smem_raw[];
+    C *ex = reinterpret_cast<C *>(smem_raw);  // [COLS*LSTEP][EX]
+    const int kx0 = blockIdx.x * COLS;
+    const int g = blockIdx.y;
+    const int r_begin = g * layers_per_group;
+    const int r_end = min(nz, r_begin + layers_per_group);
+    const int t = threadIdx.x;
+    const bool owner = t < COLS * R1;
+    const int oc = owner ? t / R1 : 0, oj = owner ? t - oc * R1 : 0;
+    const int okx = kx0 + oc;
+    C acc[R2], tw[R2];
+#pragma unroll
+    for (int s = 0; s < R2; ++s) {
+        acc[s] = c_make<C>(0, 0);
+        tw[s] = twg[s * oj];  // exp(-2 pi i s j / N), s * j < N
+    }
+    for (int r = r_begin; r < r_end; r += LSTEP) {
+        for (int it = t; it < COLS * LSTEP * R2; it += blockDim.x) {
+            const int c = it / (LSTEP * R2);
+            const int rem = it - c * (LSTEP * R2);
+            const int l = rem / R2, j = rem - l * R2;
+            const int kx = kx0 + c, rl = r + l;
+            const bool valid = kx < Kx && rl < r_end;
+            const C *col = A + ((size_t)(valid ? kx : 0) * nz + (valid ? rl : 0)) * ny;
+            C v[R1];
+#pragma unroll
+            for (int rr = 0; rr < R1; ++rr) {
+                const int q = j + R2 * rr;
+                v[rr] = (valid && q < ny) ? col[q] : c_make<C>(0, 0);
+            }
+            pass1_store<R1, false>(v, ex + (c * LSTEP + l) * EX, j);
+        }
+        __syncthreads();
+        if (owner && okx < Kx) {
+#pragma unroll
+            for (int l = 0; l < LSTEP; ++l) {
+                const int rl = r + l;
+                if (rl < r_end) {
+                    const C *Sr = S + ((size_t)okx * nz + rl) * N + oj;
+                    C sv[R2];
+#pragma unroll
+                    for (int s = 0; s < R2; ++s) sv[s] = Sr[R1 * s];
+                    C v[R2];
+                    pass2_gather<R1, R2>(v, ex + (oc * LSTEP + l) * EX, oj);
+#pragma unroll
+                    for (int s = 1; s < R2; ++s) v[s] = c_mul(v[s], tw[s]);
+                    cl::Dft<R2, false>::run(v);
+#pragma unroll
+                    for (int s = 0; s < R2; ++s) acc[s] = c_add(acc[s], c_mul(v[s], sv[s]));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (owner && okx < Kx) {
+        C *o = part + ((size_t)g * Kx + okx) * N + oj;
+#pragma unroll
+        for (int s = 0; s < R2; ++s) o[R1 * s] = acc[s];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Sum of the layer-group partials and the inverse column transform (N = R1*R2 = N'_y,
+// inverse radices (R2, R1)).  Writes B[kx][j] = IFFT_y(SUM_g part[g][kx])[j], j < sy.
+template <typename C, int R1, int R2, int COLS>
+__global__ void __launch_bounds__(256) k_cols_inv_sum(const C *__restrict__ part, int ngroups, C *__restrict__ B,
+                                                      int Kx, int sy, const C *__restrict__ twg) {
+    // inverse transform with pass-1 radix IR1 = R2 and pass-2 radix IR2 = R1
+    constexpr int IR1 = R2, IR2 = R1, N = R1 * R2, EX = Ex<IR1, IR2>::value;
+    extern __shared__ unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *ex = tw + N;  // [COLS][EX]
+    const int kx0 = blockIdx.x * COLS;
+    load_table(tw, twg, N);
+    for (int it = threadIdx.x; it < COLS * IR2; it += blockDim.x) {
+        const int c = it / IR2, j = it - c * IR2;  // pass-1 item j < IR2 takes y[j + IR2*rr], rr < IR1
+        const int kx = kx0 + c;
+        C v[IR1];
+#pragma unroll
+        for (int rr = 0; rr < IR1; ++rr) v[rr] = c_make<C>(0, 0);
+        if (kx < Kx) {
+            for (int g = 0; g < ngroups; ++g) {
+                const C *pg = part + ((size_t)g * Kx + kx) * N + j;
+#pragma unroll
+                for (int rr = 0; rr < IR1; ++rr) v[rr] = c_add(v[rr], pg[IR2 * rr]);
+            }
+        }
+        pass1_store<IR1, true>(v, ex + c * EX, j);
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < COLS * IR1; it += blockDim.x) {
+        const int c = it / IR1, j = it - c * IR1;
+        const int kx = kx0 + c;
+        C v[IR2];
+        pass2_gather<IR1, IR2>(v, ex + c * EX, j);
+        pass2_twiddle_table<IR1, IR2, true>(v, tw, j);
+        cl::Dft<IR2, true>::run(v);
+        if (kx < Kx) {
+            C *o = B + (size_t)kx * sy;
+#pragma unroll
+            for (int s = 0; s < IR2; ++s) {
+                const int q = j + IR1 * s;
+                if (q < sy) o[q] = v[s];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Transpose column pass (N = R1*R2 = N'_y).  Block (column group, layer group):
+// Dh = FFT_y(D1[kx][0:sy]) once (radices (R1, R2)); its pass-2 owners (c, j) keep
+// Dh[j + R1*s] in registers; then for each layer the inverse transform (radices (R2, R1))
+// of conj(S[kx][r]) * Dh starts from exactly those values, and A2[kx][r][q] = result[q], q < ny.
+template <typename C, int R1, int R2, int COLS, int LSTEP>
+__global__ void __launch_bounds__(COLS * R1 <= 256 ? 256 : 512)
+    k_cols_tr(const C *__restrict__ D1, const C *__restrict__ S, C *__restrict__ A2, int Kx, int nz, int ny, int sy,
+              int layers_per_group, const C *__restrict__ twg) {
+    constexpr int N = R1 * R2;
+    constexpr int EXF = Ex<R1, R2>::value;  // forward exchange (pass-1 radix R1)
+    constexpr int EXI = Ex<R2, R1>::value;  // inverse exchange (pass-1 radix R2)
+    constexpr int EXM = EXF > EXI ? EXF : EXI;
+    extern __shared__ unsigned char smem_raw[];
+    C *tw = reinterpret_cast<C *>(smem_raw);
+    C *ex = tw + N;  // [COLS*LSTEP][EXM]
+    const int kx0 = blockIdx.x * COLS;
+    const int g = blockIdx.y;
+    const int r_begin = g * layers_per_group;
+    const int r_end = min(nz, r_begin + layers_per_group);
+    const int t = threadIdx.x;
+    const bool owner = t < COLS * R1;
+    const int oc = owner ? t / R1 : 0, oj = owner ? t - oc * R1 : 0;
+    const int okx = kx0 + oc;
+    load_table(tw, twg, N);
+    // forward transform of the data columns: pass 1 items j < R2 take D1[kx][j + R2*rr]
+    for (int it = t; it < COLS * R2; it += blockDim.x) {
+        const int c = it / R2, j = it - c * R2;
+        const int kx = kx0 + c;
+        const C *col = D1 + (size_t)(kx < Kx ? kx : 0) * sy;
+        C v[R1];
+#pragma unroll
+        for (int rr = 0; rr < R1; ++rr) {
+            const int q = j + R2 * rr;
+            v[rr] = (kx < Kx && q < sy) ? col[q] : c_make<C>(0, 0);
+        }
+        pass1_store<R1, false>(v, ex + c * EXM, j);
+    }
+    __syncthreads();
+    C dh[R2];
+    if (owner) {
+        pass2_gather<R1, R2>(dh, ex + oc * EXM, oj);
+        pass2_twiddle_table<R1, R2, false>(dh, tw, oj);
+        cl::Dft<R2, false>::run(dh);
+    }
+    __syncthreads();
+    for (int r = r_begin; r < r_end; r += LSTEP) {
+        // inverse pass 1 (radix R2) by the owners: y[oj + R1*rr] = conj(S) * Dh, rr < R2
+        if (owner && okx < Kx) {
+#pragma unroll
+            for (int l = 0; l < LSTEP; ++l) {
+                const int rl = r + l;
+                if (rl < r_end) {
+                    const C *Sr = S + ((size_t)okx * nz + rl) * N + oj;
+                    C v[R2];
+#pragma unroll
+                    for (int s = 0; s < R2; ++s) v[s] = c_mulc(dh[s], Sr[R1 * s]);
+                    pass1_store<R2, true>(v, ex + (oc * LSTEP + l) * EXM, oj);
+                }
+            }
+        }
+        __syncthreads();
+        // inverse pass 2 (radix R1): items j < R2, outputs q = j + R2*s (s < R1), q < ny
+        for (int it = t; it < COLS * LSTEP * R2; it += blockDim.x) {
+            const int c = it / (LSTEP * R2);
+            const int rem = it - c * (LSTEP * R2);
+            const int l = rem / R2, j = rem - l * R2;
+            const int kx = kx0 + c, rl = r + l;
+            if (kx >= Kx || rl >= r_end) continue;
+            C v[R1];
+            pass2_gather<R2, R1>(v, ex + (c * LSTEP + l) * EXM, j);
+            pass2_twiddle_table<R2, R1, true>(v, tw, j);
+            cl::Dft<R1, true>::run(v);
+            C *o = A2 + ((size_t)kx * nz + rl) * ny;
+#pragma unroll
+            for (int s = 0; s < R1; ++s) {
+                const int q = j + R2 * s;
+                if (q < ny) o[q] = v[s];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace fast
+}  // namespace gm

@@ -35,6 +35,12 @@ struct gm_plan {
     void *stage_m = nullptr, *stage_d = nullptr;
     size_t work_bytes = 0;
 
+    // Register-codelet path (apply_fast.cu): used when both FFT lengths have instantiations.
+    bool fast = false;
+    void *work_part = nullptr;          // [groups][Kx][NPy] partial depth sums of the forward pass
+    int fast_groups_fwd = 1, fast_lpg_fwd = 1;
+    int fast_groups_tr = 1, fast_lpg_tr = 1;
+
     // CGLS scratch, allocated on the first gm_cgls call.
     void *cgls_buf = nullptr;
     size_t cgls_bytes = 0;
@@ -52,7 +58,7 @@ namespace gm {
 // Kernel ids for the timing table.
 enum KernelId {
     K_FWD_ROWS = 0, K_FWD_COLS = 1, K_FWD_C2R = 2, K_TR_ROWS = 3, K_TR_COLS = 4, K_TR_C2R = 5, K_CGLS_VEC = 6,
-    K_COUNT = 7
+    K_FWD_COLS_INV = 7, K_COUNT = 8
 };
 extern const char *const kKernelNames[K_COUNT];
 
@@ -80,6 +86,12 @@ cudaError_t make_twiddles(int N, bool f64, void **dev_out);
 
 // Set-up: FP64 entries -> generators -> FP64 2-D FFT -> spectra in the plan's precision.
 cudaError_t build_spectra(gm_plan *p, cudaStream_t s);
+
+// Register-codelet apply path (apply_fast.cu).
+bool fast_path_supported(int NPx, int NPy);
+void fast_plan_groups(gm_plan *p);
+cudaError_t launch_forward_fast(gm_plan *p, const void *m, void *d, cudaStream_t s, int *nl);
+cudaError_t launch_transpose_fast(gm_plan *p, const void *d, void *m, cudaStream_t s, int *nl);
 
 // Apply launchers (forward: K4-K6, transpose: K7-K9); return the launch count in *nl.
 cudaError_t launch_forward(gm_plan *p, const void *m, void *d, cudaStream_t s, int *nl);

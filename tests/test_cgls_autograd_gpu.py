@@ -93,13 +93,15 @@ def _cpu_tikhonov(G, d, alpha):
 
 @pytest.mark.parametrize("kind", [W.GRAVITY, W.MAGNETIC])
 def test_cgls_converges_to_tikhonov_solution(gm, kind):
-    """With n = 60 unknowns, 200 CGLS iterations reach the exact regularised solution."""
+    """200 CGLS iterations reach the exact regularised solution.  alpha = 0.3 ||G|| keeps the
+    condition number of G^T G + alpha^2 I near 12, so CG's error bound (((sqrt(k)-1)/(sqrt(k)+1))^i)
+    is far below rounding after 200 iterations."""
     import torch
 
     geom = O.Geometry.uniform(4, 3, 2, 20.0, 25.0, 15.0, px=1, py=1, kind=kind, incl_deg=50.0, decl_deg=8.0)
     G = O.dense(geom)
     d = W.random_vector((3, 4), 9)
-    alpha = 0.05 * float(np.linalg.norm(G, 2))
+    alpha = 0.3 * float(np.linalg.norm(G, 2))
     x_ref = _cpu_tikhonov(G, d.ravel(), alpha)
     op = gm.Operator(4, 3, 2, 20.0, 25.0, 15.0, px=1, py=1, kind=kind, incl_deg=50.0, decl_deg=8.0,
                      precision=gm.F64)
@@ -119,12 +121,18 @@ def test_cgls_mag128_inversion(gm):
     import torch
 
     w, op32, op64, m_true, d = _mag128_problem(gm)
+    op32.forward(d.new_zeros(op32.model_shape, dtype=torch.float32))
+    n_fwd = op32.last_launch_count()
+    op32.transpose(d.float())
+    n_tr = op32.last_launch_count()
     x, res = op32.cgls(d.float(), 1e-2, 50)
     assert np.all(np.isfinite(res))
     assert res[-1] < 0.2 * res[0]
     assert np.all(np.diff(res) <= 1e-3 * res[0])  # data misfit (essentially) non-increasing
+    # the recursively updated FP32 residual drifts from the true one by O(iters * eps32 * ||d||)
     r = float((op64.forward(x.double()) - d).norm())
-    assert r == pytest.approx(res[-1], rel=2e-3)
-    assert op32.last_launch_count() == 3 + 3 + 4 + 50 * 12  # start-up + 12 launches per iteration
+    assert abs(r - res[-1]) < 1e-4 * res[0], (r, res[-1], res[0])
+    # start-up: G x0, G^T r and 4 vector kernels; per iteration: G p, G^T r and 6 vector kernels
+    assert op32.last_launch_count() == n_fwd + n_tr + 4 + 50 * (n_fwd + n_tr + 6)
     op32.close()
     op64.close()

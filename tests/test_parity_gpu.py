@@ -213,3 +213,22 @@ def test_repeated_applies_are_bitwise_deterministic(gm):
     for _ in range(3):
         assert torch.equal(op.forward(m), a)
     op.close()
+
+
+@pytest.mark.parametrize("name", ["grav16", "mag64", "grav300", "mag128", "grav64"])
+@pytest.mark.parametrize("prec", [1, 0])
+def test_codelet_path_matches_generic_path(gm, name, prec, monkeypatch):
+    """The register-codelet kernels (used for these FFT lengths) against the generic kernels
+    (selected with GM_GENERIC_FFT=1 at set-up), which the random-shape tests pin to the oracle."""
+    import torch
+
+    w = W.WORKLOADS[name]
+    m = W.model(name, 0) if name != "grav64" else W.random_vector(w.model_shape, 3)
+    d = W.data(name, 0) if name in W.WORKLOADS and name != "grav64" else W.random_vector(w.data_shape, 4)
+    monkeypatch.setenv("GM_GENERIC_FFT", "1")
+    ref_f, ref_t = run(gm, w, prec, m, d)
+    monkeypatch.delenv("GM_GENERIC_FFT")
+    got_f, got_t = run(gm, w, prec, m, d)
+    tol = 1e-13 if prec == 1 else 2e-6
+    assert rel_err(got_f, ref_f) < tol
+    assert rel_err(got_t, ref_t) < tol
