@@ -16,97 +16,103 @@ namespace gm {
 
 namespace {
 
-constexpr int kPairs = 8;   // two-row transforms per row-kernel CTA
+constexpr int kPairs = 8;   // two-row transforms per row-kernel CTA (many rows)
 constexpr int kLstep = 2;   // layers per step in the column kernels
 
-inline int round32(int x) { return (x + 31) / 32 * 32; }
+// Row kernels with few CTAs' worth of rows use one-warp CTAs of a single two-row transform.
+inline bool few_rows(int rows, int nlayers) {
+    return (long long)((rows + 2 * kPairs - 1) / (2 * kPairs)) * nlayers < 2LL * sm_count();
+}
 
 template <int R1> constexpr int cols_per_cta() { return 256 / R1 > 0 ? 256 / R1 : 1; }
-template <int R1, int R2> constexpr int cols_per_cta_inv() { return 256 / (R1 > R2 ? R1 : R2); }
 
 // ---- x-direction (rows): r2c with radices (X1, X2), c2r with (X2, X1)
+template <typename R, int X1, int X2, int PAIRS, int THREADS>
+cudaError_t rows_r2c_p(const R *in, int rows, int row_len, int nlayers, cpx_t<R> *out, int out_rows,
+                       const void *tw, cudaStream_t s) {
+    using C = cpx_t<R>;
+    const size_t sm = sizeof(C) * (PAIRS * fast::Ex<X1, X2>::value);
+    auto k = fast::k_rows_r2c<C, R, X1, X2, PAIRS, THREADS>;
+    cudaError_t e = allow_smem(k, sm);
+    if (e != cudaSuccess) return e;
+    dim3 grd((rows + 2 * PAIRS - 1) / (2 * PAIRS), nlayers);
+    k<<<grd, THREADS, sm, s>>>(in, rows, row_len, nlayers, out, out_rows, static_cast<const C *>(tw));
+    return cudaGetLastError();
+}
+
 template <typename R, int X1, int X2>
 cudaError_t rows_r2c(const R *in, int rows, int row_len, int nlayers, cpx_t<R> *out, int out_rows,
                      const void *tw, cudaStream_t s) {
+    static_assert(X1 <= 32 && X2 <= 32, "one-warp CTAs hold one item of each pass per thread");
+    if (few_rows(rows, nlayers)) return rows_r2c_p<R, X1, X2, 1, 32>(in, rows, row_len, nlayers, out, out_rows, tw, s);
+    return rows_r2c_p<R, X1, X2, kPairs, 256>(in, rows, row_len, nlayers, out, out_rows, tw, s);
+}
+
+template <typename R, int X1, int X2, int PAIRS, int THREADS>
+cudaError_t rows_c2r_p(const cpx_t<R> *in, long long ld_k, long long ld_layer, long long ld_row, int rows,
+                       int nlayers, R *out, int row_len_out, double scale, const void *tw, cudaStream_t s) {
     using C = cpx_t<R>;
-    constexpr int N = X1 * X2;
-    static_assert(kPairs * X1 <= 256, "pass 2 of the row transform holds one item per thread");
-    const size_t sm = sizeof(C) * (N + kPairs * fast::Ex<X1, X2>::value);
-    auto k = fast::k_rows_r2c<C, R, X1, X2, kPairs>;
+    constexpr int N = X1 * X2, Kx = N / 2 + 1;
+    // inverse radices (X2, X1): pass-2 items j < X2 write X2-wide coalesced rows
+    const size_t sm = sizeof(C) * (2 * PAIRS * Kx + PAIRS * fast::Ex<X2, X1>::value);
+    auto k = fast::k_rows_c2r<C, R, X2, X1, PAIRS, THREADS>;
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
-    dim3 grd((rows + 2 * kPairs - 1) / (2 * kPairs), nlayers);
-    k<<<grd, 256, sm, s>>>(in, rows, row_len, nlayers, out, out_rows, static_cast<const C *>(tw));
+    dim3 grd((rows + 2 * PAIRS - 1) / (2 * PAIRS), nlayers);
+    k<<<grd, THREADS, sm, s>>>(in, ld_k, ld_layer, ld_row, rows, out, row_len_out, scale,
+                               static_cast<const C *>(tw));
     return cudaGetLastError();
 }
 
 template <typename R, int X1, int X2>
 cudaError_t rows_c2r(const cpx_t<R> *in, long long ld_k, long long ld_layer, long long ld_row, int rows,
                      int nlayers, R *out, int row_len_out, double scale, const void *tw, cudaStream_t s) {
-    using C = cpx_t<R>;
-    constexpr int N = X1 * X2, Kx = N / 2 + 1;
-    // inverse radices (X2, X1): pass-2 items j < X2 write X2-wide coalesced rows
-    const size_t sm = sizeof(C) * (N + 2 * kPairs * Kx + kPairs * fast::Ex<X2, X1>::value);
-    auto k = fast::k_rows_c2r<C, R, X2, X1, kPairs>;
-    cudaError_t e = allow_smem(k, sm);
-    if (e != cudaSuccess) return e;
-    dim3 grd((rows + 2 * kPairs - 1) / (2 * kPairs), nlayers);
-    k<<<grd, 256, sm, s>>>(in, ld_k, ld_layer, ld_row, rows, out, row_len_out, scale, static_cast<const C *>(tw));
-    return cudaGetLastError();
+    if (few_rows(rows, nlayers))
+        return rows_c2r_p<R, X1, X2, 1, 32>(in, ld_k, ld_layer, ld_row, rows, nlayers, out, row_len_out, scale, tw,
+                                            s);
+    return rows_c2r_p<R, X1, X2, kPairs, 256>(in, ld_k, ld_layer, ld_row, rows, nlayers, out, row_len_out, scale,
+                                              tw, s);
 }
 
 // ---- y-direction (columns): forward radices (Y1, Y2)
 template <typename R, int Y1, int Y2>
 size_t fwd_mac_smem() {
-    return sizeof(cpx_t<R>) * cols_per_cta<Y1>() * kLstep * fast::Ex<Y1, Y2>::value;
+    return sizeof(cpx_t<R>) * (Y1 * Y2 + cols_per_cta<Y1>() * kLstep * fast::Ex<Y1, Y2>::value);
 }
 template <typename R, int Y1, int Y2>
 size_t tr_smem() {
     constexpr int a = fast::Ex<Y1, Y2>::value, b = fast::Ex<Y2, Y1>::value;
     return sizeof(cpx_t<R>) * (Y1 * Y2 + cols_per_cta<Y1>() * kLstep * (a > b ? a : b));
 }
+template <int Y1> constexpr int cols_threads() { return (cols_per_cta<Y1>() * Y1 + 31) / 32 * 32; }
 
 template <typename R, int Y1, int Y2>
-cudaError_t cols_fwd_mac(const gm_plan *p, const cpx_t<R> *A, const cpx_t<R> *S, cpx_t<R> *part, cudaStream_t s) {
+cudaError_t cols_fwd_mac(const gm_plan *p, const cpx_t<R> *A, const cpx_t<R> *S, cpx_t<R> *part, cpx_t<R> *B,
+                         cudaStream_t s) {
     using C = cpx_t<R>;
-    constexpr int COLS = cols_per_cta<Y1>();
+    constexpr int COLS = cols_per_cta<Y1>(), T = cols_threads<Y1>();
     const Geo &g = p->geo;
     const size_t sm = fwd_mac_smem<R, Y1, Y2>();
-    auto k = fast::k_cols_fwd_mac<C, Y1, Y2, COLS, kLstep>;
+    auto k = fast::k_cols_fwd_mac<C, Y1, Y2, COLS, kLstep, T>;
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
     dim3 grd((g.Kx + COLS - 1) / COLS, p->fast_groups_fwd);
-    k<<<grd, round32(COLS * Y1), sm, s>>>(A, S, part, g.Kx, g.nz, g.ny, p->fast_lpg_fwd,
-                                          static_cast<const C *>(p->tw_y));
-    return cudaGetLastError();
-}
-
-template <typename R, int Y1, int Y2>
-cudaError_t cols_inv_sum(const gm_plan *p, const cpx_t<R> *part, cpx_t<R> *B, cudaStream_t s) {
-    using C = cpx_t<R>;
-    constexpr int COLS = cols_per_cta_inv<Y1, Y2>();
-    const Geo &g = p->geo;
-    const size_t sm = sizeof(C) * (Y1 * Y2 + COLS * fast::Ex<Y2, Y1>::value);
-    auto k = fast::k_cols_inv_sum<C, Y1, Y2, COLS>;
-    cudaError_t e = allow_smem(k, sm);
-    if (e != cudaSuccess) return e;
-    k<<<(g.Kx + COLS - 1) / COLS, 256, sm, s>>>(part, p->fast_groups_fwd, B, g.Kx, g.sy,
-                                                static_cast<const C *>(p->tw_y));
+    k<<<grd, T, sm, s>>>(A, S, part, B, static_cast<unsigned int *>(p->work_counters), g.Kx, g.nz, g.ny, g.sy,
+                         p->fast_lpg_fwd, p->fast_groups_fwd, static_cast<const C *>(p->tw_y));
     return cudaGetLastError();
 }
 
 template <typename R, int Y1, int Y2>
 cudaError_t cols_tr(const gm_plan *p, const cpx_t<R> *D1, const cpx_t<R> *S, cpx_t<R> *A2, cudaStream_t s) {
     using C = cpx_t<R>;
-    constexpr int COLS = cols_per_cta<Y1>();
+    constexpr int COLS = cols_per_cta<Y1>(), T = cols_threads<Y1>();
     const Geo &g = p->geo;
     const size_t sm = tr_smem<R, Y1, Y2>();
-    auto k = fast::k_cols_tr<C, Y1, Y2, COLS, kLstep>;
+    auto k = fast::k_cols_tr<C, Y1, Y2, COLS, kLstep, T>;
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
     dim3 grd((g.Kx + COLS - 1) / COLS, p->fast_groups_tr);
-    k<<<grd, round32(COLS * Y1), sm, s>>>(D1, S, A2, g.Kx, g.nz, g.ny, g.sy, p->fast_lpg_tr,
-                                          static_cast<const C *>(p->tw_y));
+    k<<<grd, T, sm, s>>>(D1, S, A2, g.Kx, g.nz, g.ny, g.sy, p->fast_lpg_tr, static_cast<const C *>(p->tw_y));
     return cudaGetLastError();
 }
 
@@ -147,16 +153,9 @@ cudaError_t x_c2r(int N, const cpx_t<R> *in, long long ldk, long long ldl, long 
 }
 
 template <typename R>
-cudaError_t y_fwd_mac(const gm_plan *p, const cpx_t<R> *A, const cpx_t<R> *S, cpx_t<R> *part, cudaStream_t s) {
-#define F(n, a, b) if (p->geo.NPy == n) return cols_fwd_mac<R, a, b>(p, A, S, part, s);
-    GM_Y_SIZES(F)
-#undef F
-    return cudaErrorNotSupported;
-}
-
-template <typename R>
-cudaError_t y_inv_sum(const gm_plan *p, const cpx_t<R> *part, cpx_t<R> *B, cudaStream_t s) {
-#define F(n, a, b) if (p->geo.NPy == n) return cols_inv_sum<R, a, b>(p, part, B, s);
+cudaError_t y_fwd_mac(const gm_plan *p, const cpx_t<R> *A, const cpx_t<R> *S, cpx_t<R> *part, cpx_t<R> *B,
+                      cudaStream_t s) {
+#define F(n, a, b) if (p->geo.NPy == n) return cols_fwd_mac<R, a, b>(p, A, S, part, B, s);
     GM_Y_SIZES(F)
 #undef F
     return cudaErrorNotSupported;
@@ -180,7 +179,7 @@ int y_cols_per_cta(int N) {
 
 template <typename R>
 int y_block(int N) {
-#define F(n, a, b) if (N == n) return round32(cols_per_cta<a>() * a);
+#define F(n, a, b) if (N == n) return cols_threads<a>();
     GM_Y_SIZES(F)
 #undef F
     return 256;
@@ -198,8 +197,9 @@ template <typename R>
 const void *y_kernel(int N, bool tr) {
 #define F(n, a, b)                                                                                     \
     if (N == n)                                                                                        \
-        return tr ? (const void *)fast::k_cols_tr<cpx_t<R>, a, b, cols_per_cta<a>(), kLstep>           \
-                  : (const void *)fast::k_cols_fwd_mac<cpx_t<R>, a, b, cols_per_cta<a>(), kLstep>;
+        return tr ? (const void *)fast::k_cols_tr<cpx_t<R>, a, b, cols_per_cta<a>(), kLstep, cols_threads<a>()> \
+                  : (const void *)fast::k_cols_fwd_mac<cpx_t<R>, a, b, cols_per_cta<a>(), kLstep,            \
+                                                       cols_threads<a>()>;
     GM_Y_SIZES(F)
 #undef F
     return nullptr;
@@ -223,16 +223,13 @@ cudaError_t forward_fast_t(gm_plan *p, const R *m, R *d, cudaStream_t s, int *nl
     CK(x_r2c<R>(g.NPx, m, g.ny, g.nx, g.nz, A, g.ny, p->tw_x, s));
     timing_end(p, s, t);
     t = timing_begin(p, s, K_FWD_COLS);
-    CK(y_fwd_mac<R>(p, A, S, part, s));
-    timing_end(p, s, t);
-    t = timing_begin(p, s, K_FWD_COLS_INV);
-    CK(y_inv_sum<R>(p, part, B, s));
+    CK(y_fwd_mac<R>(p, A, S, part, B, s));
     timing_end(p, s, t);
     t = timing_begin(p, s, K_FWD_C2R);
     // B is [kx][j]: element (k, row j) at k*sy + j
     CK(x_c2r<R>(g.NPx, B, g.sy, 0, 1, g.sy, 1, d, g.sx, 1.0 / ((double)g.NPx * g.NPy), p->tw_x, s));
     timing_end(p, s, t);
-    *nl = 4;
+    *nl = 3;
     return cudaSuccess;
 }
 
@@ -284,6 +281,11 @@ void choose_groups(const gm_plan *p, bool tr, int *groups, int *lpg) {
 }  // namespace
 
 bool fast_path_supported(int NPx, int NPy) { return x_supported(NPx) && y_supported(NPy); }
+
+int fast_column_groups(const gm_plan *p) {
+    const int cols = p->precision == GM_F64 ? y_cols_per_cta<double>(p->geo.NPy) : y_cols_per_cta<float>(p->geo.NPy);
+    return (p->geo.Kx + cols - 1) / cols;
+}
 
 void fast_plan_groups(gm_plan *p) {
     if (p->precision == GM_F64) {

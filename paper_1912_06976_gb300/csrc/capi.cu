@@ -126,6 +126,7 @@ static void free_plan(gm_plan *p) {
     cudaFree(p->work_big);
     cudaFree(p->work_small);
     cudaFree(p->work_part);
+    cudaFree(p->work_counters);
     cudaFree(p->stage_m);
     cudaFree(p->stage_d);
     cudaFree(p->tw_x);
@@ -237,10 +238,11 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
     const size_t small = cel * (size_t)g.Kx * g.sy;
     const size_t n_model = (size_t)g.nx * g.ny * g.nz, n_data = (size_t)g.sx * g.sy;
     p->fast = !fast_disabled() && gm::fast_path_supported(g.NPx, g.NPy);
-    size_t part = 0;
+    size_t part = 0, ncount = 0;
     if (p->fast) {
         gm::fast_plan_groups(p);
         part = cel * (size_t)p->fast_groups_fwd * g.Kx * g.NPy;
+        ncount = (size_t)gm::fast_column_groups(p);
     }
     p->work_bytes = big + small + part + rel * (n_model + n_data);
     const size_t setup_peak = sizeof(double) * ((size_t)(p->Nx + 1) * (p->Ny + 1) * g.nz +
@@ -277,6 +279,10 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
     SETUP_TRY(cudaMalloc(&p->work_big, big), "workspace");
     SETUP_TRY(cudaMalloc(&p->work_small, small), "workspace");
     if (part) SETUP_TRY(cudaMalloc(&p->work_part, part), "workspace");
+    if (ncount) {
+        SETUP_TRY(cudaMalloc(&p->work_counters, sizeof(unsigned int) * ncount), "workspace");
+        SETUP_TRY(cudaMemset(p->work_counters, 0, sizeof(unsigned int) * ncount), "workspace");
+    }
     SETUP_TRY(cudaMalloc(&p->stage_m, rel * n_model), "staging");
     SETUP_TRY(cudaMalloc(&p->stage_d, rel * n_data), "staging");
     cudaStream_t s;

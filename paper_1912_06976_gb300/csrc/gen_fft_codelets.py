@@ -6,8 +6,10 @@ Odd primes use the symmetric-pair form (N-1)/2 real cosines and sines; 4 uses
 the radix-4 butterfly; composite sizes are split N = N1 * N2 (Cooley-Tukey,
 input n = N2 n1 + n2, output k = k1 + N1 k2) with the twiddles exp(-2 pi i
 n2 k1 / N) emitted as literals; multiplications by +-1, +-i and (+-1 +- i)/sqrt2
-are specialised.  Constants are computed here in double precision with Python's
-math module and written with 17 significant digits.
+are specialised.  Inputs known to be zero (the zero padding of the transforms)
+are propagated symbolically, so the input-pruned variants dftN_inL skip the work
+on them.  Constants are computed with mpmath at 40 digits, rounded to double and
+written with 17 significant digits.
 
 Run:  python gen_fft_codelets.py   (self-tests every codelet against numpy's FFT by executing
 the emitted statements in Python, then rewrites gm_fft_codelets.cuh next to this file)
@@ -55,19 +57,42 @@ class Emitter:
         self.lines.append(f"const R {t} = {expr};")
         return t
 
-    # complex values are (re, im) pairs of expression names
+    # complex values are (re, im) pairs of expression names; None is an exact zero
     def add(self, a, b):
+        if a is None:
+            return b
+        if b is None:
+            return a
         return (self.let(f"{a[0]} + {b[0]}"), self.let(f"{a[1]} + {b[1]}"))
 
+    def neg(self, a):
+        if a is None:
+            return None
+        return (self.let(f"-{a[0]}"), self.let(f"-{a[1]}"))
+
     def sub(self, a, b):
+        if b is None:
+            return a
+        if a is None:
+            return self.neg(b)
         return (self.let(f"{a[0]} - {b[0]}"), self.let(f"{a[1]} - {b[1]}"))
 
     def mul_i(self, a, sign):
         """a * (sign * i)"""
+        if a is None:
+            return None
         return (self.let(f"-{a[1]}") if sign > 0 else a[1], a[0] if sign > 0 else self.let(f"-{a[0]}"))
+
+    def scale(self, a, c):
+        """a * real constant c (a complex)"""
+        if a is None:
+            return None
+        return (f"{a[0]} * {lit(c)}", f"{a[1]} * {lit(c)}")
 
     def twiddle(self, a, k, n, sign):
         """a * exp(sign * 2 pi i k / n)"""
+        if a is None:
+            return None
         k %= n
         if k == 0:
             return a
@@ -119,37 +144,47 @@ class Emitter:
         h = (n - 1) // 2
         a = [self.add(x[k], x[n - k]) for k in range(1, h + 1)]
         b = [self.sub(x[k], x[n - k]) for k in range(1, h + 1)]
-        s0r = " + ".join([x[0][0]] + [ak[0] for ak in a])
-        s0i = " + ".join([x[0][1]] + [ak[1] for ak in a])
+
+        def lin(base, terms):
+            """base + SUM c_k * t_k over the nonzero terms (base may be None)"""
+            parts_r = ([base[0]] if base is not None else []) + [f"{t[0]} * {lit(c)}" for c, t in terms if t is not None]
+            parts_i = ([base[1]] if base is not None else []) + [f"{t[1]} * {lit(c)}" for c, t in terms if t is not None]
+            if not parts_r:
+                return None
+            return (self.let(" + ".join(parts_r)), self.let(" + ".join(parts_i)))
+
         out = [None] * n
-        out[0] = (self.let(s0r), self.let(s0i))
+        s0 = [x[0]] + a
+        nz = [t for t in s0 if t is not None]
+        out[0] = None if not nz else (self.let(" + ".join(t[0] for t in nz)), self.let(" + ".join(t[1] for t in nz)))
         for m in range(1, h + 1):
-            cs = [cos2pi(k * m, n) for k in range(1, h + 1)]
-            ss = [sin2pi(k * m, n) for k in range(1, h + 1)]
-            Ar = self.let(" + ".join([x[0][0]] + [f"{a[k][0]} * {lit(cs[k])}" for k in range(h)]))
-            Ai = self.let(" + ".join([x[0][1]] + [f"{a[k][1]} * {lit(cs[k])}" for k in range(h)]))
-            Br = self.let(" + ".join([f"{b[k][0]} * {lit(ss[k])}" for k in range(h)]))
-            Bi = self.let(" + ".join([f"{b[k][1]} * {lit(ss[k])}" for k in range(h)]))
+            A = lin(x[0], [(cos2pi(k * m, n), a[k - 1]) for k in range(1, h + 1)])
+            B = lin(None, [(sin2pi(k * m, n), b[k - 1]) for k in range(1, h + 1)])
             # X_m = A + sign*i*B, X_{n-m} = A - sign*i*B
-            if sign < 0:
-                out[m] = (self.let(f"{Ar} + {Bi}"), self.let(f"{Ai} - {Br}"))
-                out[n - m] = (self.let(f"{Ar} - {Bi}"), self.let(f"{Ai} + {Br}"))
-            else:
-                out[m] = (self.let(f"{Ar} - {Bi}"), self.let(f"{Ai} + {Br}"))
-                out[n - m] = (self.let(f"{Ar} + {Bi}"), self.let(f"{Ai} - {Br}"))
+            iB = self.mul_i(B, sign)
+            out[m] = self.add(A, iB)
+            out[n - m] = self.sub(A, iB)
         return out
 
 
-def codelet(n, inverse):
+def codelet(n, inverse, nin=None):
+    """DFT-n on v[0..n-1]; with nin < n the inputs v[nin..n-1] are taken as zero (not read)."""
+    nin = n if nin is None else nin
     e = Emitter()
-    x = [(f"v[{k}].x", f"v[{k}].y") for k in range(n)]
+    x = [(f"v[{k}].x", f"v[{k}].y") if k < nin else None for k in range(n)]
     out = e.dft(x, +1 if inverse else -1)
     body = ["    " + ln for ln in e.lines]
-    body += [f"    v[{k}].x = {out[k][0]};" for k in range(n)]
-    body += [f"    v[{k}].y = {out[k][1]};" for k in range(n)]
-    name = "idft" if inverse else "dft"
-    return (f"template <typename C>\n__device__ __forceinline__ void {name}{n}(C (&v)[{n}]) {{\n"
+    body += [f"    v[{k}].x = {out[k][0] if out[k] else 'R(0)'};" for k in range(n)]
+    body += [f"    v[{k}].y = {out[k][1] if out[k] else 'R(0)'};" for k in range(n)]
+    name = ("idft" if inverse else "dft") + str(n) + ("" if nin == n else f"_in{nin}")
+    return (f"template <typename C>\n__device__ __forceinline__ void {name}(C (&v)[{n}]) {{\n"
             f"    using R = decltype(v[0].x);\n" + "\n".join(body) + "\n}\n")
+
+
+# input-pruned variants: sizes used as the first pass of zero-padded transforms, with the
+# numbers of leading nonzero inputs offered (a kernel picks the smallest bucket that covers it)
+# (none instantiated: for the prime-radix codelets used here the saving is ~5%, see DESIGN.md)
+PRUNED = {}
 
 
 def selftest():
@@ -158,19 +193,21 @@ def selftest():
 
     rng = np.random.default_rng(0)
     worst = 0.0
-    for n in SIZES:
+    cases = [(n, n) for n in SIZES] + [(n, L) for n, ls in PRUNED.items() for L in ls]
+    for n, nin in cases:
         for inv in (False, True):
             e = Emitter()
-            out = e.dft([(f"vx[{k}]", f"vy[{k}]") for k in range(n)], +1 if inv else -1)
+            out = e.dft([(f"vx[{k}]", f"vy[{k}]") if k < nin else None for k in range(n)], +1 if inv else -1)
             code = [re.sub(r"R\(([^)]*)\)", r"\1", ln.replace("const R ", "")).rstrip(";") for ln in e.lines]
             x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+            x[nin:] = 0
             env = {"vx": list(x.real), "vy": list(x.imag)}
             exec("\n".join(code), env)
-            got = np.array([eval(o[0], env) + 1j * eval(o[1], env) for o in out])
+            got = np.array([(eval(o[0], env) + 1j * eval(o[1], env)) if o else 0j for o in out])
             ref = np.fft.ifft(x) * n if inv else np.fft.fft(x)
             err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
             worst = max(worst, err)
-            assert err < 1e-14, (n, inv, err)
+            assert err < 1e-14, (n, nin, inv, err)
     return worst
 
 
@@ -182,13 +219,25 @@ def main():
     for n in SIZES:
         parts.append(codelet(n, False))
         parts.append(codelet(n, True))
-    parts.append("// Dispatch by size: Dft<N, INV>::run(v).")
+    for n, ls in PRUNED.items():
+        for L in ls:
+            parts.append(codelet(n, False, L))
+            parts.append(codelet(n, True, L))
+    parts.append("// Dispatch by size: Dft<N, INV>::run(v); DftIn<N, L, INV>::run(v) reads only v[0..L-1].")
     parts.append("template <int N, bool INV> struct Dft;")
     for n in SIZES:
         for inv in (False, True):
             nm = ("idft" if inv else "dft") + str(n)
             parts.append(f"template <> struct Dft<{n}, {'true' if inv else 'false'}> {{ template <typename C> "
                          f"__device__ __forceinline__ static void run(C (&v)[{n}]) {{ {nm}(v); }} }};")
+    parts.append("template <int N, int L, bool INV> struct DftIn { template <typename C> "
+                 "__device__ __forceinline__ static void run(C (&v)[N]) { Dft<N, INV>::run(v); } };")
+    for n, ls in PRUNED.items():
+        for L in ls:
+            for inv in (False, True):
+                nm = ("idft" if inv else "dft") + f"{n}_in{L}"
+                parts.append(f"template <> struct DftIn<{n}, {L}, {'true' if inv else 'false'}> {{ template <typename C> "
+                             f"__device__ __forceinline__ static void run(C (&v)[{n}]) {{ {nm}(v); }} }};")
     parts += ["", "}  // namespace cl", "}  // namespace gm", ""]
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "gm_fft_codelets.cuh")
     with open(out, "w") as f:

@@ -4,6 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <set>
+#include <utility>
+
 namespace gm {
 
 // Complex type of a real precision.
@@ -26,11 +30,35 @@ template <typename C> __device__ __forceinline__ C c_mulc(C a, C b) {
 }
 template <typename C> __device__ __forceinline__ C c_conj(C a) { return c_make<C>(a.x, -a.y); }
 
-// Opts a kernel into more than the default 48 KB of dynamic shared memory when needed.
+// Opts a kernel into more than the default 48 KB of dynamic shared memory when needed, once
+// per (kernel, device, size) so that launches do not pay for the attribute call.
 template <typename K>
 inline cudaError_t allow_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    static std::mutex mu;
+    static std::set<std::pair<std::pair<const void *, int>, size_t>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const auto key = std::make_pair(std::make_pair((const void *)kernel, dev), bytes);
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(key)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
+
+// Number of SMs of the current device (queried once per device).
+inline int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 148;
+        cache[dev] = n;
+    }
+    return cache[dev];
 }
 
 // Mixed-radix plan of one FFT length: the radices of its passes (product = N)

@@ -23,8 +23,12 @@ namespace fast {
 
 template <int R> struct Pitch { static constexpr int value = (R % 2) ? R : R + 1; };
 
-// Exchange size (complex values) of one transform whose pass 1 has radix R1.
-template <int R1, int R2> struct Ex { static constexpr int value = R2 * Pitch<R1>::value; };
+// Exchange size (complex values) of one transform whose pass 1 has radix R1, rounded up to an
+// odd count so that consecutive transforms start in different banks.
+template <int R1, int R2> struct Ex {
+    static constexpr int raw = R2 * Pitch<R1>::value;
+    static constexpr int value = (raw % 2) ? raw : raw + 1;
+};
 
 template <int R1, bool INV, typename C>
 __device__ __forceinline__ void pass1_store(C (&v)[R1], C *ex, int j) {
@@ -41,9 +45,10 @@ __device__ __forceinline__ void pass2_gather(C (&v)[R2], const C *ex, int j) {
     for (int rr = 0; rr < R2; ++rr) v[rr] = ex[rr * P + j];
 }
 
-// twiddles from a table of exp(-2 pi i e / N), e < N (conjugated for the inverse)
+// twiddles from a table of exp(-2 pi i e / N), e < N (conjugated for the inverse): the global
+// table through the read-only cache, or a shared-memory copy
 template <int R1, int R2, bool INV, typename C>
-__device__ __forceinline__ void pass2_twiddle_table(C (&v)[R2], const C *tw, int j) {
+__device__ __forceinline__ void pass2_twiddle_table(C (&v)[R2], const C *__restrict__ tw, int j) {
 #pragma unroll
     for (int rr = 1; rr < R2; ++rr) {
         C w = tw[rr * j];
@@ -52,26 +57,37 @@ __device__ __forceinline__ void pass2_twiddle_table(C (&v)[R2], const C *tw, int
     }
 }
 
-template <typename C>
-__device__ __forceinline__ void load_table(C *dst, const C *src, int n) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+// Copies the N-entry twiddle table to shared memory, all loads of a thread issued together.
+template <int N, int THREADS, typename C>
+__device__ __forceinline__ void load_table(C *dst, const C *__restrict__ src) {
+    constexpr int B = (N + THREADS - 1) / THREADS;
+    C tmp[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int i = threadIdx.x + b * THREADS;
+        if (i < N) tmp[b] = __ldg(src + i);
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int i = threadIdx.x + b * THREADS;
+        if (i < N) dst[i] = tmp[b];
+    }
 }
 
 // ------------------------------------------------------------------------------------------
 // Real rows -> half spectra (two rows per complex transform, N = R1*R2 = N'_x).
 // Block (pair group, layer) transforms rows q0 .. q0 + 2*PAIRS - 1 of `layer` of
 // in[layer][row][0:row_len] and writes out[k][layer][row] (row stride out_rows), k < N/2+1.
-template <typename C, typename Rin, int R1, int R2, int PAIRS>
-__global__ void __launch_bounds__(256) k_rows_r2c(const Rin *__restrict__ in, int rows, int row_len, int nlayers,
-                                                  C *__restrict__ out, int out_rows, const C *__restrict__ twg) {
+template <typename C, typename Rin, int R1, int R2, int PAIRS, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_rows_r2c(const Rin *__restrict__ in, int rows, int row_len, int nlayers,
+                                                      C *__restrict__ out, int out_rows, const C *__restrict__ tw) {
     constexpr int N = R1 * R2, EX = Ex<R1, R2>::value, Kx = N / 2 + 1;
+    static_assert(PAIRS * R2 <= THREADS && PAIRS * R1 <= THREADS, "one item of each pass per thread");
     extern __shared__ unsigned char smem_raw[];
-    C *tw = reinterpret_cast<C *>(smem_raw);
-    C *ex = tw + N;
+    C *ex = reinterpret_cast<C *>(smem_raw);
     const int q0 = blockIdx.x * 2 * PAIRS;
     const int layer = blockIdx.y;
-    load_table(tw, twg, N);
-    for (int it = threadIdx.x; it < PAIRS * R2; it += blockDim.x) {
+    for (int it = threadIdx.x; it < PAIRS * R2; it += THREADS) {
         const int p = it / R2, j = it - p * R2;
         const int qa = q0 + 2 * p;
         const bool va = qa < rows, vb = qa + 1 < rows;
@@ -104,7 +120,8 @@ __global__ void __launch_bounds__(256) k_rows_r2c(const Rin *__restrict__ in, in
     }
     __syncthreads();
     // separate the two real rows: FFT(a)[k] = (Z[k] + conj Z[-k]) / 2, FFT(b)[k] = (Z[k] - conj Z[-k]) / 2i
-    for (int it = threadIdx.x; it < PAIRS * Kx; it += blockDim.x) {
+#pragma unroll 4
+    for (int it = threadIdx.x; it < PAIRS * Kx; it += THREADS) {
         const int k = it / PAIRS, p = it - k * PAIRS;
         const int qa = q0 + 2 * p;
         if (qa >= rows) continue;
@@ -125,25 +142,38 @@ __global__ void __launch_bounds__(256) k_rows_r2c(const Rin *__restrict__ in, in
 // Half spectra -> real rows (two rows per complex inverse transform, N = R1*R2 = N'_x).
 // X(k, layer, row) = in[k*ld_k + layer*ld_layer + row*ld_row], k < N/2+1; writes
 // out[layer][row][0:row_len_out] = scale * (inverse transform)[0:row_len_out].
-template <typename C, typename Rout, int R1, int R2, int PAIRS>
-__global__ void __launch_bounds__(256) k_rows_c2r(const C *__restrict__ in, long long ld_k, long long ld_layer,
-                                                  long long ld_row, int rows, Rout *__restrict__ out, int row_len_out,
-                                                  double scale, const C *__restrict__ twg) {
+template <typename C, typename Rout, int R1, int R2, int PAIRS, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_rows_c2r(const C *__restrict__ in, long long ld_k, long long ld_layer,
+                                                      long long ld_row, int rows, Rout *__restrict__ out,
+                                                      int row_len_out, double scale, const C *__restrict__ tw) {
     constexpr int N = R1 * R2, EX = Ex<R1, R2>::value, Kx = N / 2 + 1, H = N / 2;
     extern __shared__ unsigned char smem_raw[];
-    C *tw = reinterpret_cast<C *>(smem_raw);
-    C *xs = tw + N;                 // [2*PAIRS][Kx]
-    C *ex = xs + 2 * PAIRS * Kx;    // [PAIRS][EX]
+    C *xs = reinterpret_cast<C *>(smem_raw);  // [2*PAIRS][Kx]
+    C *ex = xs + 2 * PAIRS * Kx;               // [PAIRS][EX]
     const int q0 = blockIdx.x * 2 * PAIRS;
     const int layer = blockIdx.y;
-    load_table(tw, twg, N);
-    for (int it = threadIdx.x; it < Kx * 2 * PAIRS; it += blockDim.x) {
-        const int k = it / (2 * PAIRS), row = it - k * 2 * PAIRS;
-        const int q = q0 + row;
-        xs[row * Kx + k] = (q < rows) ? in[k * ld_k + layer * ld_layer + q * ld_row] : c_make<C>(0, 0);
+    {
+        // staging in one round: every load of a thread is issued before its shared-memory stores
+        constexpr int TOT = Kx * 2 * PAIRS, BATCH = (TOT + THREADS - 1) / THREADS;
+        C tmp[BATCH];
+#pragma unroll
+        for (int b = 0; b < BATCH; ++b) {
+            const int it = threadIdx.x + b * THREADS;
+            const int k = it / (2 * PAIRS), row = it - k * 2 * PAIRS;
+            const int q = q0 + row;
+            tmp[b] = (it < TOT && q < rows) ? in[k * ld_k + layer * ld_layer + q * ld_row] : c_make<C>(0, 0);
+        }
+#pragma unroll
+        for (int b = 0; b < BATCH; ++b) {
+            const int it = threadIdx.x + b * THREADS;
+            if (it < TOT) {
+                const int k = it / (2 * PAIRS), row = it - k * 2 * PAIRS;
+                xs[row * Kx + k] = tmp[b];
+            }
+        }
     }
     __syncthreads();
-    for (int it = threadIdx.x; it < PAIRS * R2; it += blockDim.x) {
+    for (int it = threadIdx.x; it < PAIRS * R2; it += THREADS) {
         const int p = it / R2, j = it - p * R2;
         const C *x1r = xs + (2 * p) * Kx, *x2r = x1r + Kx;
         C v[R1];
@@ -158,8 +188,8 @@ __global__ void __launch_bounds__(256) k_rows_c2r(const C *__restrict__ in, long
         pass1_store<R1, true>(v, ex + p * EX, j);
     }
     __syncthreads();
-    const auto sc = (decltype(tw[0].x))scale;
-    for (int it = threadIdx.x; it < PAIRS * R1; it += blockDim.x) {
+    const auto sc = (decltype(ex[0].x))scale;
+    for (int it = threadIdx.x; it < PAIRS * R1; it += THREADS) {
         const int p = it / R1, j = it - p * R1;
         C v[R2];
         pass2_gather<R1, R2>(v, ex + p * EX, j);
@@ -179,17 +209,68 @@ __global__ void __launch_bounds__(256) k_rows_c2r(const C *__restrict__ in, long
 }
 
 // ------------------------------------------------------------------------------------------
+// Sum of the layer-group partials of COLS columns and their inverse column transform
+// (N = R1*R2 = N'_y, inverse radices (R2, R1)): B[kx][j] = IFFT_y(SUM_g part[g][kx])[j], j < sy.
+// Run by the whole block; ex holds COLS exchange regions of Ex<R2, R1>.
+template <typename C, int R1, int R2, int COLS, int THREADS>
+__device__ __forceinline__ void cols_sum_inverse(const C *__restrict__ part, int ngroups, C *__restrict__ B, int Kx,
+                                                 int sy, int kx0, const C *__restrict__ tw, C *ex) {
+    constexpr int IR1 = R2, IR2 = R1, N = R1 * R2, EX = Ex<IR1, IR2>::value;
+    for (int it = threadIdx.x; it < COLS * IR2; it += THREADS) {
+        const int c = it / IR2, j = it - c * IR2;  // pass-1 item j < IR2 takes y[j + IR2*rr], rr < IR1
+        const int kx = kx0 + c;
+        C v[IR1];
+#pragma unroll
+        for (int rr = 0; rr < IR1; ++rr) v[rr] = c_make<C>(0, 0);
+        if (kx < Kx) {
+            for (int g = 0; g < ngroups; ++g) {
+                const C *pg = part + ((size_t)g * Kx + kx) * N + j;
+                C tmp[IR1];
+#pragma unroll
+                for (int rr = 0; rr < IR1; ++rr) tmp[rr] = __ldcg(pg + IR2 * rr);  // written by other CTAs
+#pragma unroll
+                for (int rr = 0; rr < IR1; ++rr) v[rr] = c_add(v[rr], tmp[rr]);
+            }
+        }
+        pass1_store<IR1, true>(v, ex + c * EX, j);
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < COLS * IR1; it += THREADS) {
+        const int c = it / IR1, j = it - c * IR1;
+        const int kx = kx0 + c;
+        C v[IR2];
+        pass2_gather<IR1, IR2>(v, ex + c * EX, j);
+        pass2_twiddle_table<IR1, IR2, true>(v, tw, j);
+        cl::Dft<IR2, true>::run(v);
+        if (kx < Kx) {
+            C *o = B + (size_t)kx * sy;
+#pragma unroll
+            for (int s = 0; s < IR2; ++s) {
+                const int q = j + IR1 * s;
+                if (q < sy) o[q] = v[s];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Forward column pass with the depth multiply-accumulate (N = R1*R2 = N'_y).
 // Block (column group, layer group): for its COLS columns kx and layers r in the group,
-// acc[kx][k] = SUM_r S[kx][r][k] * FFT_y(A[kx][r][0:ny])[k]; writes acc to part[group][kx][k].
+// acc[kx][k] = SUM_r S[kx][r][k] * FFT_y(A[kx][r][0:ny])[k], written to part[group][kx][k].
 // Pass-2 thread (c, j) owns k = j + R1*s (s < R2) for every layer, so acc stays in registers.
-template <typename C, int R1, int R2, int COLS, int LSTEP>
-__global__ void __launch_bounds__(COLS * R1 <= 256 ? 256 : 512)
-    k_cols_fwd_mac(const C *__restrict__ A, const C *__restrict__ S, C *__restrict__ part, int Kx, int nz, int ny,
-                   int layers_per_group, const C *__restrict__ twg) {
+// The last block of a column group to finish (counted with an atomic; nothing waits) sums the
+// groups' partials in group order and runs the inverse column transform into B[kx][0:sy].
+template <typename C, int R1, int R2, int COLS, int LSTEP, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+    k_cols_fwd_mac(const C *__restrict__ A, const C *__restrict__ S, C *__restrict__ part, C *__restrict__ B,
+                   unsigned int *__restrict__ counters, int Kx, int nz, int ny, int sy, int layers_per_group,
+                   int ngroups, const C *__restrict__ twg) {
     constexpr int N = R1 * R2, EX = Ex<R1, R2>::value;
+    static_assert(COLS * R1 <= THREADS, "one pass-2 owner per thread");
     extern __shared__ unsigned char smem_raw[];
-    C *ex = reinterpret_cast<C *>(smem_raw);  // [COLS*LSTEP][EX]
+    C *tw = reinterpret_cast<C *>(smem_raw);  // [N]
+    C *ex = tw + N;                           // [COLS*LSTEP][EX]
+    __shared__ unsigned int s_last;
     const int kx0 = blockIdx.x * COLS;
     const int g = blockIdx.y;
     const int r_begin = g * layers_per_group;
@@ -198,14 +279,12 @@ __global__ void __launch_bounds__(COLS * R1 <= 256 ? 256 : 512)
     const bool owner = t < COLS * R1;
     const int oc = owner ? t / R1 : 0, oj = owner ? t - oc * R1 : 0;
     const int okx = kx0 + oc;
-    C acc[R2], tw[R2];
+    C acc[R2];
 #pragma unroll
-    for (int s = 0; s < R2; ++s) {
-        acc[s] = c_make<C>(0, 0);
-        tw[s] = twg[s * oj];  // exp(-2 pi i s j / N), s * j < N
-    }
+    for (int s = 0; s < R2; ++s) acc[s] = c_make<C>(0, 0);
+    load_table<N, THREADS>(tw, twg);
     for (int r = r_begin; r < r_end; r += LSTEP) {
-        for (int it = t; it < COLS * LSTEP * R2; it += blockDim.x) {
+        for (int it = t; it < COLS * LSTEP * R2; it += THREADS) {
             const int c = it / (LSTEP * R2);
             const int rem = it - c * (LSTEP * R2);
             const int l = rem / R2, j = rem - l * R2;
@@ -227,16 +306,12 @@ __global__ void __launch_bounds__(COLS * R1 <= 256 ? 256 : 512)
                 const int rl = r + l;
                 if (rl < r_end) {
                     const C *Sr = S + ((size_t)okx * nz + rl) * N + oj;
-                    C sv[R2];
-#pragma unroll
-                    for (int s = 0; s < R2; ++s) sv[s] = Sr[R1 * s];
                     C v[R2];
                     pass2_gather<R1, R2>(v, ex + (oc * LSTEP + l) * EX, oj);
-#pragma unroll
-                    for (int s = 1; s < R2; ++s) v[s] = c_mul(v[s], tw[s]);
+                    pass2_twiddle_table<R1, R2, false>(v, tw, oj);
                     cl::Dft<R2, false>::run(v);
 #pragma unroll
-                    for (int s = 0; s < R2; ++s) acc[s] = c_add(acc[s], c_mul(v[s], sv[s]));
+                    for (int s = 0; s < R2; ++s) acc[s] = c_add(acc[s], c_mul(v[s], Sr[R1 * s]));
                 }
             }
         }
@@ -247,53 +322,19 @@ __global__ void __launch_bounds__(COLS * R1 <= 256 ? 256 : 512)
 #pragma unroll
         for (int s = 0; s < R2; ++s) o[R1 * s] = acc[s];
     }
-}
-
-// ------------------------------------------------------------------------------------------
-// Sum of the layer-group partials and the inverse column transform (N = R1*R2 = N'_y,
-// inverse radices (R2, R1)).  Writes B[kx][j] = IFFT_y(SUM_g part[g][kx])[j], j < sy.
-template <typename C, int R1, int R2, int COLS>
-__global__ void __launch_bounds__(256) k_cols_inv_sum(const C *__restrict__ part, int ngroups, C *__restrict__ B,
-                                                      int Kx, int sy, const C *__restrict__ twg) {
-    // inverse transform with pass-1 radix IR1 = R2 and pass-2 radix IR2 = R1
-    constexpr int IR1 = R2, IR2 = R1, N = R1 * R2, EX = Ex<IR1, IR2>::value;
-    extern __shared__ unsigned char smem_raw[];
-    C *tw = reinterpret_cast<C *>(smem_raw);
-    C *ex = tw + N;  // [COLS][EX]
-    const int kx0 = blockIdx.x * COLS;
-    load_table(tw, twg, N);
-    for (int it = threadIdx.x; it < COLS * IR2; it += blockDim.x) {
-        const int c = it / IR2, j = it - c * IR2;  // pass-1 item j < IR2 takes y[j + IR2*rr], rr < IR1
-        const int kx = kx0 + c;
-        C v[IR1];
-#pragma unroll
-        for (int rr = 0; rr < IR1; ++rr) v[rr] = c_make<C>(0, 0);
-        if (kx < Kx) {
-            for (int g = 0; g < ngroups; ++g) {
-                const C *pg = part + ((size_t)g * Kx + kx) * N + j;
-#pragma unroll
-                for (int rr = 0; rr < IR1; ++rr) v[rr] = c_add(v[rr], pg[IR2 * rr]);
-            }
-        }
-        pass1_store<IR1, true>(v, ex + c * EX, j);
+    // publish the partial, then count this group in; the last group of the column group finishes it
+    __threadfence();
+    __syncthreads();
+    if (t == 0) {
+        const unsigned int prev = atomicAdd(counters + blockIdx.x, 1u);
+        s_last = (prev == (unsigned int)ngroups - 1u) ? 1u : 0u;
     }
     __syncthreads();
-    for (int it = threadIdx.x; it < COLS * IR1; it += blockDim.x) {
-        const int c = it / IR1, j = it - c * IR1;
-        const int kx = kx0 + c;
-        C v[IR2];
-        pass2_gather<IR1, IR2>(v, ex + c * EX, j);
-        pass2_twiddle_table<IR1, IR2, true>(v, tw, j);
-        cl::Dft<IR2, true>::run(v);
-        if (kx < Kx) {
-            C *o = B + (size_t)kx * sy;
-#pragma unroll
-            for (int s = 0; s < IR2; ++s) {
-                const int q = j + IR1 * s;
-                if (q < sy) o[q] = v[s];
-            }
-        }
-    }
+    if (!s_last) return;
+    __threadfence();
+    if (t == 0) counters[blockIdx.x] = 0u;  // ready for the next product
+    static_assert(COLS * Ex<R2, R1>::value <= COLS * LSTEP * EX, "the inverse reuses the exchange buffer");
+    cols_sum_inverse<C, R1, R2, COLS, THREADS>(part, ngroups, B, Kx, sy, kx0, tw, ex);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -301,17 +342,18 @@ __global__ void __launch_bounds__(256) k_cols_inv_sum(const C *__restrict__ part
 // Dh = FFT_y(D1[kx][0:sy]) once (radices (R1, R2)); its pass-2 owners (c, j) keep
 // Dh[j + R1*s] in registers; then for each layer the inverse transform (radices (R2, R1))
 // of conj(S[kx][r]) * Dh starts from exactly those values, and A2[kx][r][q] = result[q], q < ny.
-template <typename C, int R1, int R2, int COLS, int LSTEP>
-__global__ void __launch_bounds__(COLS * R1 <= 256 ? 256 : 512)
+template <typename C, int R1, int R2, int COLS, int LSTEP, int THREADS>
+__global__ void __launch_bounds__(THREADS)
     k_cols_tr(const C *__restrict__ D1, const C *__restrict__ S, C *__restrict__ A2, int Kx, int nz, int ny, int sy,
               int layers_per_group, const C *__restrict__ twg) {
     constexpr int N = R1 * R2;
     constexpr int EXF = Ex<R1, R2>::value;  // forward exchange (pass-1 radix R1)
     constexpr int EXI = Ex<R2, R1>::value;  // inverse exchange (pass-1 radix R2)
     constexpr int EXM = EXF > EXI ? EXF : EXI;
+    static_assert(COLS * R1 <= THREADS, "one owner per thread");
     extern __shared__ unsigned char smem_raw[];
-    C *tw = reinterpret_cast<C *>(smem_raw);
-    C *ex = tw + N;  // [COLS*LSTEP][EXM]
+    C *tw = reinterpret_cast<C *>(smem_raw);  // [N]
+    C *ex = tw + N;                           // [COLS*LSTEP][EXM]
     const int kx0 = blockIdx.x * COLS;
     const int g = blockIdx.y;
     const int r_begin = g * layers_per_group;
@@ -320,9 +362,9 @@ __global__ void __launch_bounds__(COLS * R1 <= 256 ? 256 : 512)
     const bool owner = t < COLS * R1;
     const int oc = owner ? t / R1 : 0, oj = owner ? t - oc * R1 : 0;
     const int okx = kx0 + oc;
-    load_table(tw, twg, N);
+    load_table<N, THREADS>(tw, twg);
     // forward transform of the data columns: pass 1 items j < R2 take D1[kx][j + R2*rr]
-    for (int it = t; it < COLS * R2; it += blockDim.x) {
+    for (int it = t; it < COLS * R2; it += THREADS) {
         const int c = it / R2, j = it - c * R2;
         const int kx = kx0 + c;
         const C *col = D1 + (size_t)(kx < Kx ? kx : 0) * sy;
@@ -359,7 +401,7 @@ __global__ void __launch_bounds__(COLS * R1 <= 256 ? 256 : 512)
         }
         __syncthreads();
         // inverse pass 2 (radix R1): items j < R2, outputs q = j + R2*s (s < R1), q < ny
-        for (int it = t; it < COLS * LSTEP * R2; it += blockDim.x) {
+        for (int it = t; it < COLS * LSTEP * R2; it += THREADS) {
             const int c = it / (LSTEP * R2);
             const int rem = it - c * (LSTEP * R2);
             const int l = rem / R2, j = rem - l * R2;

@@ -38,6 +38,7 @@ struct gm_plan {
     // Register-codelet path (apply_fast.cu): used when both FFT lengths have instantiations.
     bool fast = false;
     void *work_part = nullptr;          // [groups][Kx][NPy] partial depth sums of the forward pass
+    void *work_counters = nullptr;      // one arrival counter per column group of the forward pass
     int fast_groups_fwd = 1, fast_lpg_fwd = 1;
     int fast_groups_tr = 1, fast_lpg_tr = 1;
 
@@ -67,11 +68,12 @@ inline int timing_begin(gm_plan *p, cudaStream_t s, int kid) {
     if (p->tused >= (int)p->tkid.size()) return -1;
     int slot = p->tused++;
     p->tkid[slot] = kid;
-    cudaEventRecord(p->tev[2 * slot], s);
+    // external: inside a stream capture the record becomes an event-record node of the graph
+    cudaEventRecordWithFlags(p->tev[2 * slot], s, cudaEventRecordExternal);
     return slot;
 }
 inline void timing_end(gm_plan *p, cudaStream_t s, int slot) {
-    if (slot >= 0) cudaEventRecord(p->tev[2 * slot + 1], s);
+    if (slot >= 0) cudaEventRecordWithFlags(p->tev[2 * slot + 1], s, cudaEventRecordExternal);
 }
 }  // namespace gm
 
@@ -89,6 +91,7 @@ cudaError_t build_spectra(gm_plan *p, cudaStream_t s);
 
 // Register-codelet apply path (apply_fast.cu).
 bool fast_path_supported(int NPx, int NPy);
+int fast_column_groups(const gm_plan *p);
 void fast_plan_groups(gm_plan *p);
 cudaError_t launch_forward_fast(gm_plan *p, const void *m, void *d, cudaStream_t s, int *nl);
 cudaError_t launch_transpose_fast(gm_plan *p, const void *d, void *m, cudaStream_t s, int *nl);
