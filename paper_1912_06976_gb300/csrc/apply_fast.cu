@@ -75,8 +75,17 @@ cudaError_t rows_c2r(const cpx_t<R> *in, long long ld_k, long long ld_layer, lon
 }
 
 // ---- y-direction (columns): forward radices (Y1, Y2)
+template <int Y1> constexpr int cols_threads() { return (cols_per_cta<Y1>() * Y1 + 31) / 32 * 32; }
+
+template <typename R, int Y1, int Y2> struct ColCfg {
+    static constexpr int COLS = cols_per_cta<Y1>();
+    static constexpr int T_FWD = cols_threads<Y1>();
+    static constexpr int COLS_TR = cols_per_cta<Y1>();
+    static constexpr int T_TR = cols_threads<Y1>();
+};
+
 template <typename R, int Y1, int Y2>
-size_t fwd_mac_smem() {
+size_t fwd_mac_smem(int) {
     return sizeof(cpx_t<R>) * (Y1 * Y2 + cols_per_cta<Y1>() * kLstep * fast::Ex<Y1, Y2>::value);
 }
 template <typename R, int Y1, int Y2>
@@ -84,35 +93,49 @@ size_t tr_smem() {
     constexpr int a = fast::Ex<Y1, Y2>::value, b = fast::Ex<Y2, Y1>::value;
     return sizeof(cpx_t<R>) * (Y1 * Y2 + cols_per_cta<Y1>() * kLstep * (a > b ? a : b));
 }
-template <int Y1> constexpr int cols_threads() { return (cols_per_cta<Y1>() * Y1 + 31) / 32 * 32; }
+
+template <typename R, int Y1, int Y2>
+const void *fwd_kernel() {
+    using CC = ColCfg<R, Y1, Y2>;
+    return (const void *)fast::k_cols_fwd_mac<cpx_t<R>, Y1, Y2, CC::COLS, kLstep, CC::T_FWD>;
+}
+template <typename R, int Y1, int Y2>
+const void *tr_kernel() {
+    using CC = ColCfg<R, Y1, Y2>;
+    return (const void *)fast::k_cols_tr<cpx_t<R>, Y1, Y2, CC::COLS_TR, kLstep, CC::T_TR>;
+}
 
 template <typename R, int Y1, int Y2>
 cudaError_t cols_fwd_mac(const gm_plan *p, const cpx_t<R> *A, const cpx_t<R> *S, cpx_t<R> *part, cpx_t<R> *B,
                          cudaStream_t s) {
     using C = cpx_t<R>;
-    constexpr int COLS = cols_per_cta<Y1>(), T = cols_threads<Y1>();
+    using CC = ColCfg<R, Y1, Y2>;
+    constexpr int COLS = CC::COLS, T = CC::T_FWD;
     const Geo &g = p->geo;
-    const size_t sm = fwd_mac_smem<R, Y1, Y2>();
-    auto k = fast::k_cols_fwd_mac<C, Y1, Y2, COLS, kLstep, T>;
+    const size_t sm = fwd_mac_smem<R, Y1, Y2>(g.nyp);
+    auto k = reinterpret_cast<void (*)(const C *, const C *, C *, C *, unsigned int *, int, int, int, int, int, int,
+                                       int, const C *)>(const_cast<void *>(fwd_kernel<R, Y1, Y2>()));
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
     dim3 grd((g.Kx + COLS - 1) / COLS, p->fast_groups_fwd);
-    k<<<grd, T, sm, s>>>(A, S, part, B, static_cast<unsigned int *>(p->work_counters), g.Kx, g.nz, g.ny, g.sy,
-                         p->fast_lpg_fwd, p->fast_groups_fwd, static_cast<const C *>(p->tw_y));
+    k<<<grd, T, sm, s>>>(A, S, part, B, static_cast<unsigned int *>(p->work_counters), g.Kx, g.nz, g.ny, g.nyp,
+                         g.sy, p->fast_lpg_fwd, p->fast_groups_fwd, static_cast<const C *>(p->tw_y));
     return cudaGetLastError();
 }
 
 template <typename R, int Y1, int Y2>
 cudaError_t cols_tr(const gm_plan *p, const cpx_t<R> *D1, const cpx_t<R> *S, cpx_t<R> *A2, cudaStream_t s) {
     using C = cpx_t<R>;
-    constexpr int COLS = cols_per_cta<Y1>(), T = cols_threads<Y1>();
+    using CC = ColCfg<R, Y1, Y2>;
+    constexpr int COLS = CC::COLS_TR, T = CC::T_TR;
     const Geo &g = p->geo;
     const size_t sm = tr_smem<R, Y1, Y2>();
-    auto k = fast::k_cols_tr<C, Y1, Y2, COLS, kLstep, T>;
+    auto k = reinterpret_cast<void (*)(const C *, const C *, C *, int, int, int, int, int, int, const C *)>(
+        const_cast<void *>(tr_kernel<R, Y1, Y2>()));
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
     dim3 grd((g.Kx + COLS - 1) / COLS, p->fast_groups_tr);
-    k<<<grd, T, sm, s>>>(D1, S, A2, g.Kx, g.nz, g.ny, g.sy, p->fast_lpg_tr, static_cast<const C *>(p->tw_y));
+    k<<<grd, T, sm, s>>>(D1, S, A2, g.Kx, g.nz, g.ny, g.nyp, g.sy, p->fast_lpg_tr, static_cast<const C *>(p->tw_y));
     return cudaGetLastError();
 }
 
@@ -170,24 +193,24 @@ cudaError_t y_tr(const gm_plan *p, const cpx_t<R> *D1, const cpx_t<R> *S, cpx_t<
 }
 
 template <typename R>
-int y_cols_per_cta(int N) {
-#define F(n, a, b) if (N == n) return cols_per_cta<a>();
+int y_cols_per_cta(int N, bool tr = false) {
+#define F(n, a, b) if (N == n) return tr ? ColCfg<R, a, b>::COLS_TR : ColCfg<R, a, b>::COLS;
     GM_Y_SIZES(F)
 #undef F
     return 1;
 }
 
 template <typename R>
-int y_block(int N) {
-#define F(n, a, b) if (N == n) return cols_threads<a>();
+int y_block(int N, bool tr) {
+#define F(n, a, b) if (N == n) return tr ? ColCfg<R, a, b>::T_TR : ColCfg<R, a, b>::T_FWD;
     GM_Y_SIZES(F)
 #undef F
     return 256;
 }
 
 template <typename R>
-size_t y_smem(int N, bool tr) {
-#define F(n, a, b) if (N == n) return tr ? tr_smem<R, a, b>() : fwd_mac_smem<R, a, b>();
+size_t y_smem(int N, bool tr, int nyp) {
+#define F(n, a, b) if (N == n) return tr ? tr_smem<R, a, b>() : fwd_mac_smem<R, a, b>(nyp);
     GM_Y_SIZES(F)
 #undef F
     return 0;
@@ -197,9 +220,7 @@ template <typename R>
 const void *y_kernel(int N, bool tr) {
 #define F(n, a, b)                                                                                     \
     if (N == n)                                                                                        \
-        return tr ? (const void *)fast::k_cols_tr<cpx_t<R>, a, b, cols_per_cta<a>(), kLstep, cols_threads<a>()> \
-                  : (const void *)fast::k_cols_fwd_mac<cpx_t<R>, a, b, cols_per_cta<a>(), kLstep,            \
-                                                       cols_threads<a>()>;
+        return tr ? tr_kernel<R, a, b>() : fwd_kernel<R, a, b>();
     GM_Y_SIZES(F)
 #undef F
     return nullptr;
@@ -220,7 +241,7 @@ cudaError_t forward_fast_t(gm_plan *p, const R *m, R *d, cudaStream_t s, int *nl
     C *part = static_cast<C *>(p->work_part);
     const C *S = static_cast<const C *>(p->spec);
     int t = timing_begin(p, s, K_FWD_ROWS);
-    CK(x_r2c<R>(g.NPx, m, g.ny, g.nx, g.nz, A, g.ny, p->tw_x, s));
+    CK(x_r2c<R>(g.NPx, m, g.ny, g.nx, g.nz, A, g.nyp, p->tw_x, s));
     timing_end(p, s, t);
     t = timing_begin(p, s, K_FWD_COLS);
     CK(y_fwd_mac<R>(p, A, S, part, B, s));
@@ -247,8 +268,8 @@ cudaError_t transpose_fast_t(gm_plan *p, const R *d, R *m, cudaStream_t s, int *
     CK(y_tr<R>(p, D1, S, A2, s));
     timing_end(p, s, t);
     t = timing_begin(p, s, K_TR_C2R);
-    // A2 is [kx][r][q]: element (k, layer r, row q) at (k*nz + r)*ny + q
-    CK(x_c2r<R>(g.NPx, A2, (long long)g.nz * g.ny, g.ny, 1, g.ny, g.nz, m, g.nx, 1.0 / ((double)g.NPx * g.NPy),
+    // A2 is [kx][r][q] with column pitch nyp: element (k, layer r, row q) at (k*nz + r)*nyp + q
+    CK(x_c2r<R>(g.NPx, A2, (long long)g.nz * g.nyp, g.nyp, 1, g.ny, g.nz, m, g.nx, 1.0 / ((double)g.NPx * g.NPy),
                 p->tw_x, s));
     timing_end(p, s, t);
     *nl = 3;
@@ -262,12 +283,13 @@ void choose_groups(const gm_plan *p, bool tr, int *groups, int *lpg) {
     int dev = 0, sms = 1, occ = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int cols = y_cols_per_cta<R>(g.NPy);
+    const int cols = y_cols_per_cta<R>(g.NPy, tr);
     const void *k = y_kernel<R>(g.NPy, tr);
-    const size_t sm = y_smem<R>(g.NPy, tr);
+    const size_t sm = y_smem<R>(g.NPy, tr, g.nyp);
     if (k) {
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, y_block<R>(g.NPy), sm) != cudaSuccess || occ < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, y_block<R>(g.NPy, tr), sm) != cudaSuccess ||
+            occ < 1)
             occ = 1;
     }
     cudaGetLastError();

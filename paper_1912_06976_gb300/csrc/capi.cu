@@ -201,6 +201,7 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
     p->pxr = prm->pxr; p->pyr = prm->pyr;
     g.nx = prm->sx + prm->pxl + prm->pxr;
     g.ny = prm->sy + prm->pyl + prm->pyr;
+    g.nyp = g.ny + (g.ny & 1);
     p->Nx = g.sx + g.nx - 1;
     p->Ny = g.sy + g.ny - 1;
     g.NPx = gm_fft_length(p->Nx);
@@ -234,7 +235,7 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
     const size_t rel = prm->precision == GM_F64 ? sizeof(double) : sizeof(float);
     const size_t nspec = (size_t)g.Kx * g.nz * g.NPy;
     p->spec_bytes = cel * nspec;
-    const size_t big = cel * (size_t)g.Kx * g.nz * g.ny;
+    const size_t big = cel * (size_t)g.Kx * g.nz * g.nyp;
     const size_t small = cel * (size_t)g.Kx * g.sy;
     const size_t n_model = (size_t)g.nx * g.ny * g.nz, n_data = (size_t)g.sx * g.sy;
     p->fast = !fast_disabled() && gm::fast_path_supported(g.NPx, g.NPy);

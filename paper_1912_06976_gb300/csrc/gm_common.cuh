@@ -76,6 +76,7 @@ struct Geo {
     int sx, sy, nz, nx, ny;     // stations, layers, padded cells
     int pxl, pyl;               // left padding
     int NPx, NPy, Kx;           // FFT lengths, kept x-columns N'_x/2+1
+    int nyp;                    // ny rounded up to even: column pitch of the [kx][r][q] intermediates
 };
 
 // Batched in-place-ish Stockham autosort FFT on shared memory, all threads of

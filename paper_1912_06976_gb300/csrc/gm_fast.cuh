@@ -30,6 +30,12 @@ template <int R1, int R2> struct Ex {
     static constexpr int value = (raw % 2) ? raw : raw + 1;
 };
 
+// Asks the memory system to bring `bytes` (a multiple of 16) at a 16-byte aligned global address
+// into L2; fire-and-forget, nothing waits on it.
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned int bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <int R1, bool INV, typename C>
 __device__ __forceinline__ void pass1_store(C (&v)[R1], C *ex, int j) {
     cl::Dft<R1, INV>::run(v);
@@ -263,8 +269,8 @@ __device__ __forceinline__ void cols_sum_inverse(const C *__restrict__ part, int
 template <typename C, int R1, int R2, int COLS, int LSTEP, int THREADS>
 __global__ void __launch_bounds__(THREADS)
     k_cols_fwd_mac(const C *__restrict__ A, const C *__restrict__ S, C *__restrict__ part, C *__restrict__ B,
-                   unsigned int *__restrict__ counters, int Kx, int nz, int ny, int sy, int layers_per_group,
-                   int ngroups, const C *__restrict__ twg) {
+                   unsigned int *__restrict__ counters, int Kx, int nz, int ny, int nyp, int sy,
+                   int layers_per_group, int ngroups, const C *__restrict__ twg) {
     constexpr int N = R1 * R2, EX = Ex<R1, R2>::value;
     static_assert(COLS * R1 <= THREADS, "one pass-2 owner per thread");
     extern __shared__ unsigned char smem_raw[];
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(THREADS)
             const int l = rem / R2, j = rem - l * R2;
             const int kx = kx0 + c, rl = r + l;
             const bool valid = kx < Kx && rl < r_end;
-            const C *col = A + ((size_t)(valid ? kx : 0) * nz + (valid ? rl : 0)) * ny;
+            const C *col = A + ((size_t)(valid ? kx : 0) * nz + (valid ? rl : 0)) * nyp;
             C v[R1];
 #pragma unroll
             for (int rr = 0; rr < R1; ++rr) {
@@ -344,8 +350,8 @@ __global__ void __launch_bounds__(THREADS)
 // of conj(S[kx][r]) * Dh starts from exactly those values, and A2[kx][r][q] = result[q], q < ny.
 template <typename C, int R1, int R2, int COLS, int LSTEP, int THREADS>
 __global__ void __launch_bounds__(THREADS)
-    k_cols_tr(const C *__restrict__ D1, const C *__restrict__ S, C *__restrict__ A2, int Kx, int nz, int ny, int sy,
-              int layers_per_group, const C *__restrict__ twg) {
+    k_cols_tr(const C *__restrict__ D1, const C *__restrict__ S, C *__restrict__ A2, int Kx, int nz, int ny, int nyp,
+              int sy, int layers_per_group, const C *__restrict__ twg) {
     constexpr int N = R1 * R2;
     constexpr int EXF = Ex<R1, R2>::value;  // forward exchange (pass-1 radix R1)
     constexpr int EXI = Ex<R2, R1>::value;  // inverse exchange (pass-1 radix R2)
@@ -362,6 +368,11 @@ __global__ void __launch_bounds__(THREADS)
     const bool owner = t < COLS * R1;
     const int oc = owner ? t / R1 : 0, oj = owner ? t - oc * R1 : 0;
     const int okx = kx0 + oc;
+    if (t < COLS * LSTEP) {
+        const int c = t / LSTEP, l = t - c * LSTEP;
+        const int kx = kx0 + c, rn = r_begin + l;
+        if (kx < Kx && rn < r_end) prefetch_l2(S + ((size_t)kx * nz + rn) * N, (unsigned int)(sizeof(C) * N));
+    }
     load_table<N, THREADS>(tw, twg);
     // forward transform of the data columns: pass 1 items j < R2 take D1[kx][j + R2*rr]
     for (int it = t; it < COLS * R2; it += THREADS) {
@@ -385,6 +396,11 @@ __global__ void __launch_bounds__(THREADS)
     }
     __syncthreads();
     for (int r = r_begin; r < r_end; r += LSTEP) {
+        if (t < COLS * LSTEP) {
+            const int c = t / LSTEP, l = t - c * LSTEP;
+            const int kx = kx0 + c, rn = r + LSTEP + l;
+            if (kx < Kx && rn < r_end) prefetch_l2(S + ((size_t)kx * nz + rn) * N, (unsigned int)(sizeof(C) * N));
+        }
         // inverse pass 1 (radix R2) by the owners: y[oj + R1*rr] = conj(S) * Dh, rr < R2
         if (owner && okx < Kx) {
 #pragma unroll
@@ -411,7 +427,7 @@ __global__ void __launch_bounds__(THREADS)
             pass2_gather<R2, R1>(v, ex + (c * LSTEP + l) * EXM, j);
             pass2_twiddle_table<R2, R1, true>(v, tw, j);
             cl::Dft<R1, true>::run(v);
-            C *o = A2 + ((size_t)kx * nz + rl) * ny;
+            C *o = A2 + ((size_t)kx * nz + rl) * nyp;
 #pragma unroll
             for (int s = 0; s < R1; ++s) {
                 const int q = j + R2 * s;
