@@ -1,0 +1,125 @@
+"""Pins of the warm-start network oracle against definitions that do not go through it."""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import warmstart_net as N
+
+
+def brute_conv(x, w, b, stride, pad):
+    """Cross-correlation by explicit loops: out[co, o] = b[co] + sum w[co, ci, t] x[ci, o*s + t - p]."""
+    ci_, d, h, wd = x.shape
+    co_, _, kd, kh, kw = w.shape
+    od = (d + 2 * pad[0] - kd) // stride[0] + 1
+    oh = (h + 2 * pad[1] - kh) // stride[1] + 1
+    ow = (wd + 2 * pad[2] - kw) // stride[2] + 1
+    out = np.zeros((co_, od, oh, ow))
+    for co, z, y, xx in itertools.product(range(co_), range(od), range(oh), range(ow)):
+        s = b[co]
+        for ci, a, c, e in itertools.product(range(ci_), range(kd), range(kh), range(kw)):
+            iz, iy, ix = z * stride[0] + a - pad[0], y * stride[1] + c - pad[1], xx * stride[2] + e - pad[2]
+            if 0 <= iz < d and 0 <= iy < h and 0 <= ix < wd:
+                s += w[co, ci, a, c, e] * x[ci, iz, iy, ix]
+        out[co, z, y, xx] = s
+    return out
+
+
+@pytest.mark.parametrize("stride,kd", [((1, 1, 1), 3), ((1, 2, 2), 1), ((1, 2, 2), 3)])
+def test_library_conv_is_the_loop_sum(stride, kd):
+    """The conv3d call the oracle uses is the cross-correlation with the stated padding/stride."""
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((2, 4, 7, 6))
+    w = rng.standard_normal((3, 2, kd, 3, 3))
+    b = rng.standard_normal(3)
+    pad = (kd // 2, 1, 1)
+    got = torch.nn.functional.conv3d(torch.as_tensor(x)[None], torch.as_tensor(w), torch.as_tensor(b),
+                                     stride=stride, padding=pad)[0].numpy()
+    assert np.allclose(got, brute_conv(x, w, b, stride, pad), rtol=0, atol=1e-12)
+
+
+def test_upsample_index_formula():
+    x = torch.arange(2 * 3 * 2 * 3 * 4, dtype=torch.float64).reshape(2, 3, 2, 3, 4)
+    y = N.upsample(x, (2, 3, 2))
+    for n, c, z, yy, xx in itertools.product(range(2), range(3), range(4), range(9), range(8)):
+        assert y[n, c, z, yy, xx] == x[n, c, z // 2, yy // 3, xx // 2]
+
+
+def test_parameter_count_and_layout():
+    assert N.num_params() == 1858849
+    p = np.arange(N.num_params(), dtype=np.float64)
+    layers = N.unpack(p)
+    assert layers[0][0].shape == (32, 1, 1, 3, 3) and layers[0][1][0] == 32 * 9
+    assert layers[-1][0].shape == (1, 16, 3, 3, 3) and layers[-1][1][0] == N.num_params() - 1
+
+
+def test_shapes_and_reshape_convention():
+    """Output shape (N, 16, S, S); the decoder's first input depth z of channel c' is encoder
+    channel 4 c' + z: a network whose encoder output is a known channel ramp shows it."""
+    S = 16
+    rng = np.random.default_rng(0)
+    p = rng.standard_normal(N.num_params()) * 0.05
+    out = N.forward(p, rng.standard_normal((2, S, S)))
+    assert out.shape == (2, 16, S, S)
+    x = torch.arange(512, dtype=torch.float64).reshape(1, 512, 1, 1, 1)
+    v = x.reshape(1, 128, 4, 1, 1)
+    for c in (0, 5, 127):
+        for z in range(4):
+            assert v[0, c, z, 0, 0] == 4 * c + z
+
+
+def test_bf16_round_known_values():
+    vals = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, 1.0 + 2 ** -9, -3.140625, 1e-40], dtype=np.float32)
+    got = N.bf16_round(vals)
+    # 1 + 2^-8: tie between 1 and 1 + 2^-7 -> even (1); 1 + 3*2^-9 above the tie -> 1 + 2^-7
+    assert got[0] == 1.0 and got[1] == 1.0 and got[2] == 1.0 + 2 ** -7 and got[3] == 1.0
+    assert got[4] == -3.140625
+    assert got[5] == 2.0 ** -133  # subnormal: 0x000116C2 rounds down to 0x00010000
+
+
+def test_gradient_matches_finite_differences():
+    """Central differences of the float64 loss along random directions (S = 16, batch 2)."""
+    S = 16
+    rng = np.random.default_rng(3)
+    p = rng.standard_normal(N.num_params()) * 0.05
+    d = rng.standard_normal((2, S, S))
+    m = rng.standard_normal((2, 16, S, S))
+    loss, g = N.loss_and_grad(p, d, m, 0.7, 1.3)
+    assert abs(loss - N.loss(p, d, m, 0.7, 1.3)) < 1e-14 * abs(loss)
+    h = 1e-5
+    for k in range(4):
+        v = np.random.default_rng((k, 9)).standard_normal(p.size)
+        v /= np.linalg.norm(v)
+        fd = (N.loss(p + h * v, d, m, 0.7, 1.3) - N.loss(p - h * v, d, m, 0.7, 1.3)) / (2 * h)
+        assert abs(fd - g @ v) <= 1e-6 * max(abs(fd), np.linalg.norm(g) * 1e-3)
+
+
+def test_gradient_of_single_weights_by_differences():
+    """Individual weights of the first, the middle (reshape-crossing) and the last layer."""
+    S = 16
+    rng = np.random.default_rng(4)
+    p = rng.standard_normal(N.num_params()) * 0.05
+    d = rng.standard_normal((1, S, S))
+    m = rng.standard_normal((1, 16, S, S))
+    _, g = N.loss_and_grad(p, d, m)
+    offs = np.cumsum([0] + [co * ci * kd * 9 + co for ci, co, kd, _, _, _ in N.LAYERS])
+    for idx in (3, offs[5] + 17, offs[8] + 5, offs[9] - 1):
+        e = np.zeros_like(p)
+        e[idx] = 1e-5
+        fd = (N.loss(p + e, d, m) - N.loss(p - e, d, m)) / 2e-5
+        assert abs(fd - g[idx]) <= 1e-6 * max(abs(fd), 1e-6)
+
+
+def test_adam_matches_scalar_rule():
+    w, g = np.array([0.5]), np.array([0.2])
+    m1 = np.zeros(1)
+    m2 = np.zeros(1)
+    w1, m1, m2 = N.adam(w, g, m1, m2, 1, 0.01)
+    # first step: mhat = g, vhat = g^2, update lr * g / (|g| + eps)
+    assert np.allclose(w1, 0.5 - 0.01 * 0.2 / (0.2 + 1e-8), rtol=0, atol=1e-15)
+    w2, _, _ = N.adam(w1, np.array([-0.1]), m1, m2, 2, 0.01)
+    a = 0.9 * 0.1 * 0.2 + 0.1 * -0.1
+    v = 0.999 * 0.001 * 0.04 + 0.001 * 0.01
+    assert np.allclose(w2, w1 - 0.01 * (a / (1 - 0.81)) / (np.sqrt(v / (1 - 0.999 ** 2)) + 1e-8), rtol=0,
+                       atol=1e-15)
