@@ -14,6 +14,7 @@ network the library adds, written with PyTorch CPU ops in float64:
            D4 up (1,2,2), 16 -> 1, no activation         (16 x S x S)
   net(d) = out_scale * f(in_scale * d)
   loss   = mean over all outputs of (f(in_scale d) - m / out_scale)^2
+           [+ lam * mean over stations of (in_scale (G net(d) - d))^2, G dense]
 
 Every convolution is a cross-correlation with "same" zero padding (1 in each
 convolved axis) and a bias.  Parameters are one flat vector: per layer, in
@@ -116,26 +117,43 @@ def forward(params, d, in_scale=1.0, out_scale=1.0) -> np.ndarray:
     return (out_scale * y).numpy()
 
 
-def loss_and_grad(params, d, m, in_scale=1.0, out_scale=1.0):
-    """(loss, gradient with respect to the flat parameter vector), float64."""
+def _data_term(y, d, in_scale, out_scale, G):
+    """mean over examples and stations of (in_scale (G m_pred - d))^2, m_pred = out_scale y, with G
+    a dense (S*S) x (16*S*S) matrix in the layouts d[j][i] and m[r][q][p] (x fastest)."""
+    Gt = torch.as_tensor(np.asarray(G, dtype=np.float64))
+    mp = (out_scale * y).reshape(y.shape[0], -1)
+    r = in_scale * (mp @ Gt.T - d.reshape(d.shape[0], -1))
+    return (r ** 2).mean()
+
+
+def loss_and_grad(params, d, m, in_scale=1.0, out_scale=1.0, G=None, lam=0.0):
+    """(loss, gradient with respect to the flat parameter vector), float64.  With G and lam > 0
+    the loss adds lam times the data term of ``_data_term``."""
     p = torch.tensor(np.asarray(params, dtype=np.float64), requires_grad=True)
     layers, off = [], 0
     for ci, co, kd, _, _, _ in LAYERS:
         nw = co * ci * kd * 9
         layers.append((p[off:off + nw].reshape(co, ci, kd, 3, 3), p[off + nw:off + nw + co]))
         off += nw + co
-    y = f_scaled(layers, torch.as_tensor(np.asarray(d, dtype=np.float64)), in_scale)
+    dt = torch.as_tensor(np.asarray(d, dtype=np.float64))
+    y = f_scaled(layers, dt, in_scale)
     t = torch.as_tensor(np.asarray(m, dtype=np.float64)) / out_scale
     loss = ((y - t) ** 2).mean()
+    if lam > 0:
+        loss = loss + lam * _data_term(y, dt, in_scale, out_scale, G)
     loss.backward()
     return loss.item(), p.grad.numpy().copy()
 
 
-def loss(params, d, m, in_scale=1.0, out_scale=1.0) -> float:
+def loss(params, d, m, in_scale=1.0, out_scale=1.0, G=None, lam=0.0) -> float:
     with torch.no_grad():
-        y = f_scaled(unpack(params), torch.as_tensor(np.asarray(d, dtype=np.float64)), in_scale)
+        dt = torch.as_tensor(np.asarray(d, dtype=np.float64))
+        y = f_scaled(unpack(params), dt, in_scale)
         t = torch.as_tensor(np.asarray(m, dtype=np.float64)) / out_scale
-        return float(((y - t) ** 2).mean())
+        v = ((y - t) ** 2).mean()
+        if lam > 0:
+            v = v + lam * _data_term(y, dt, in_scale, out_scale, G)
+        return float(v)
 
 
 def adam(w, g, m1, m2, step, lr, b1=0.9, b2=0.999, eps=1e-8):

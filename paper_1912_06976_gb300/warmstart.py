@@ -1,0 +1,337 @@
+"""Learned warm start for the Tikhonov CGLS inversion of gravity data.
+
+A convolutional network (2-D encoder, 3-D decoder; the architecture and its
+C ABI are in include/gm_warmstart.h) maps a data grid d[S][S] to a density
+model m[16][S][S].  It is trained on pairs (m, G m + 1% noise) whose data come
+from this library's FP32 forward product, and its prediction x0 = net(d)
+starts gm_cgls.  CGLS from x0 = 0 stays the fallback and the judge: the
+comparison reports the data misfit plain CGLS reaches and the iterations and
+G / G^T applies the warm-started CGLS needs to reach it.
+
+The paper has no network; it names the inversion these products serve as the
+use of its fast operators (Sec. 1, Sec. 6).  Everything numeric here runs in
+libgravmag.so: the network's forward, backward and Adam kernels, the forward
+products that make the training data, and CGLS.  This module marshals
+arguments, draws the seeded synthetic models and keeps the training loop.
+"""
+from __future__ import annotations
+
+import concurrent.futures
+import ctypes
+import math
+import threading
+
+import numpy as np
+
+from . import gravmag as G
+from . import workloads as W
+
+DEPTH = 16
+_sig_lock = threading.Lock()
+_sig_done = False
+
+
+def _lib():
+    global _sig_done
+    lib = G.load()
+    with _sig_lock:
+        if not _sig_done:
+            vp, ci, cf, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_int64
+            sig = {
+                "gm_net_create": (vp, [ci, ci, ci, ctypes.c_ulonglong]),
+                "gm_net_destroy": (ci, [vp]),
+                "gm_net_num_params": (i64, [vp]),
+                "gm_net_set_scales": (ci, [vp, cf, cf]),
+                "gm_net_forward": (ci, [vp, vp, vp, ci, vp]),
+                "gm_net_train_step": (ci, [vp, vp, vp, ci, vp, ci, cf, ctypes.POINTER(cf), vp]),
+                "gm_net_get_params": (ci, [vp, vp, i64, ci]),
+                "gm_net_set_params": (ci, [vp, vp, i64, ci]),
+                "gm_net_get_step": (ci, [vp, ctypes.POINTER(i64)]),
+                "gm_net_set_step": (ci, [vp, i64]),
+                "gm_net_last_launch_count": (ci, [vp]),
+                "gm_net_set_data_term": (ci, [vp, vp, cf]),
+                "gm_net_last_losses": (ci, [vp, ctypes.POINTER(cf), ctypes.POINTER(cf)]),
+                "gm_net_last_error": (ctypes.c_char_p, []),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _sig_done = True
+    return lib
+
+
+def _check(status):
+    if status != G.GM_OK:
+        raise G.GravMagError(status, _lib().gm_net_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _device_f32(t, shape, name):
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return _ptr(t)
+
+
+class WarmStartNet:
+    """The network behind gm_net_*: FP32 master weights, BF16 convolution weights, Adam state."""
+
+    PARAM_WHICH = {"weights": 0, "grad": 1, "adam_m": 2, "adam_v": 3}
+
+    def __init__(self, grid: int = 64, max_batch: int = 32, seed: int = 0):
+        h = _lib().gm_net_create(int(grid), DEPTH, int(max_batch), ctypes.c_ulonglong(seed))
+        if not h:
+            raise G.GravMagError(G.GM_EINVAL, _lib().gm_net_last_error().decode(errors="replace"))
+        self._h = ctypes.c_void_p(h)
+        self.grid, self.max_batch = int(grid), int(max_batch)
+        self.in_scale, self.out_scale = 1.0, 1.0
+
+    @property
+    def num_params(self) -> int:
+        return int(_lib().gm_net_num_params(self._h))
+
+    def set_scales(self, in_scale: float, out_scale: float) -> None:
+        _check(_lib().gm_net_set_scales(self._h, float(in_scale), float(out_scale)))
+        self.in_scale, self.out_scale = float(in_scale), float(out_scale)
+
+    def forward(self, d, out=None, stream=None):
+        """net(d) for d of shape (B, S, S) -> (B, 16, S, S), float32 CUDA tensors."""
+        import torch
+
+        if d.dim() == 2:
+            return self.forward(d.unsqueeze(0), None if out is None else out.unsqueeze(0), stream)[0]
+        b = int(d.shape[0])
+        if out is None:
+            out = torch.empty((b, DEPTH, self.grid, self.grid), dtype=torch.float32, device=d.device)
+        _check(_lib().gm_net_forward(self._h, _device_f32(d, (b, self.grid, self.grid), "d"),
+                                     _device_f32(out, (b, DEPTH, self.grid, self.grid), "out"), b,
+                                     G._stream_ptr(stream)))
+        return out
+
+    def train_step(self, d, m, lr: float, index=None, stream=None, want_loss: bool = True):
+        """Loss and gradient on one batch, then an Adam step when lr > 0; returns the loss.
+
+        Without `index`, d (B, S, S) and m (B, 16, S, S) are the batch; with it (a contiguous
+        int32 CUDA tensor of B example numbers), d and m are whole example sets and the batch is
+        gathered from them inside the network's input kernels."""
+        import torch
+
+        if index is None:
+            b = int(d.shape[0])
+            ip = None
+        else:
+            if not (index.is_cuda and index.dtype == torch.int32 and index.is_contiguous() and index.dim() == 1):
+                raise TypeError("index must be a contiguous 1-D int32 CUDA tensor")
+            b = int(index.shape[0])
+            ip = _ptr(index)
+        count = int(d.shape[0])
+        if int(m.shape[0]) != count:
+            raise ValueError("d and m hold different numbers of examples")
+        loss = ctypes.c_float(0.0)
+        _check(_lib().gm_net_train_step(self._h, _device_f32(d, (count, self.grid, self.grid), "d"),
+                                        _device_f32(m, (count, DEPTH, self.grid, self.grid), "m"), count, ip, b,
+                                        float(lr), ctypes.byref(loss) if want_loss else None,
+                                        G._stream_ptr(stream)))
+        return float(loss.value) if want_loss else None
+
+    def set_data_term(self, op, lam: float) -> None:
+        """Add lam * mean((in_scale (G net(d) - d))^2) to the training loss, with G = op (an FP32
+        operator on the network's grid, S x S stations, no padding, 16 layers); lam = 0 removes it."""
+        _check(_lib().gm_net_set_data_term(self._h, op.handle if op is not None else None, float(lam)))
+        self._op = op if lam > 0 else None  # keep the operator alive while the network uses it
+
+    def last_losses(self):
+        """(model term, data term) of the last train step that read its loss back."""
+        a, b = ctypes.c_float(0), ctypes.c_float(0)
+        _check(_lib().gm_net_last_losses(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return float(a.value), float(b.value)
+
+    def get_params(self, which: str = "weights") -> np.ndarray:
+        out = np.empty(self.num_params, dtype=np.float32)
+        _check(_lib().gm_net_get_params(self._h, ctypes.c_void_p(out.ctypes.data), out.size,
+                                        self.PARAM_WHICH[which]))
+        return out
+
+    def set_params(self, values, which: str = "weights") -> None:
+        a = np.ascontiguousarray(np.asarray(values, dtype=np.float32))
+        _check(_lib().gm_net_set_params(self._h, ctypes.c_void_p(a.ctypes.data), a.size, self.PARAM_WHICH[which]))
+
+    @property
+    def step(self) -> int:
+        s = ctypes.c_int64(0)
+        _check(_lib().gm_net_get_step(self._h, ctypes.byref(s)))
+        return int(s.value)
+
+    def last_launch_count(self) -> int:
+        return int(_lib().gm_net_last_launch_count(self._h))
+
+    def save(self, path: str) -> None:
+        """Checkpoint: weights, Adam moments, step count and scales (numpy .npz)."""
+        np.savez(path, weights=self.get_params("weights"), adam_m=self.get_params("adam_m"),
+                 adam_v=self.get_params("adam_v"), step=self.step, grid=self.grid,
+                 scales=np.array([self.in_scale, self.out_scale]))
+
+    def load(self, path: str) -> None:
+        """Resume from save(): the next train_step continues the same Adam trajectory."""
+        z = np.load(path)
+        if int(z["grid"]) != self.grid:
+            raise ValueError(f"checkpoint grid {int(z['grid'])} != {self.grid}")
+        self.set_params(z["weights"], "weights")
+        self.set_params(z["adam_m"], "adam_m")
+        self.set_params(z["adam_v"], "adam_v")
+        _check(_lib().gm_net_set_step(self._h, int(z["step"])))
+        self.set_scales(*[float(v) for v in z["scales"]])
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib().gm_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------------------------------
+# training data: seeded models, their FP32 forward data plus noise
+
+def training_models(count: int, seed: int, shape=(DEPTH, 64, 64), threads: int = 0) -> np.ndarray:
+    """`count` models (float32, (count, 16, S, S)); model i is drawn from rng (seed, i, 0x57) so the
+    set does not depend on the thread count."""
+    out = np.empty((count,) + tuple(shape), dtype=np.float32)
+
+    def one(i):
+        out[i] = W.training_model(np.random.default_rng((seed, i, 0x57)), shape)
+
+    threads = threads or min(16, max(1, (__import__("os").cpu_count() or 1)))
+    with concurrent.futures.ThreadPoolExecutor(threads) as ex:
+        list(ex.map(one, range(count)))
+    return out
+
+
+def make_data(op: "G.Operator", models, noise_level: float, seed: int):
+    """d_i = G m_i (this library's FP32 forward) + Gaussian noise of standard deviation
+    noise_level * rms(G m_i), noise drawn from rng (seed, i, 0x4E).  `models` is a float32 CUDA
+    tensor (count, 16, S, S); returns (clean, noisy) float32 CUDA tensors (count, S, S) and the
+    noisy set on the host (float64)."""
+    import torch
+
+    count = int(models.shape[0])
+    clean = torch.empty((count,) + tuple(op.data_shape), dtype=torch.float32, device=models.device)
+    for i in range(count):
+        op.forward(models[i], out=clean[i])
+    host = clean.cpu().numpy().astype(np.float64)
+    noisy = np.empty_like(host)
+    for i in range(count):
+        rms = float(np.sqrt(np.mean(host[i] ** 2)))
+        noisy[i] = host[i] + np.random.default_rng((seed, i, 0x4E)).standard_normal(host[i].shape) * (
+            noise_level * rms)
+    return clean, torch.as_tensor(noisy.astype(np.float32)).to(models.device), noisy
+
+
+def fit_scales(models: np.ndarray, data: np.ndarray):
+    """in_scale = 1 / rms(data), out_scale = rms(models), over the training set."""
+    return 1.0 / float(np.sqrt(np.mean(np.square(data, dtype=np.float64)))), \
+        float(np.sqrt(np.mean(np.square(models, dtype=np.float64))))
+
+
+def train(net: WarmStartNet, models, data, steps: int, batch: int, lr: float = 1e-3, seed: int = 0,
+          lr_final: float | None = None, log_every: int = 0, record_every_loss: bool = True, stream=None):
+    """Adam on minibatches drawn without replacement from a seeded permutation per epoch (the
+    gather runs inside the network's input kernels); the learning rate decays by a cosine from
+    lr to lr_final (default lr / 20).  Returns the loss of every step (None where not read back:
+    reading it synchronises)."""
+    import torch
+
+    count = int(models.shape[0])
+    if batch > net.max_batch or batch > count:
+        raise ValueError("batch larger than the network's max_batch or the training set")
+    lr_final = lr / 20 if lr_final is None else lr_final
+    losses = []
+    perm, pos, epoch = None, count, 0
+    for k in range(steps):
+        if pos + batch > count:
+            perm = torch.as_tensor(np.random.default_rng((seed, epoch, 0xE9)).permutation(count).astype(np.int32),
+                                   device=data.device)
+            pos, epoch = 0, epoch + 1
+        rate = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * k / max(1, steps - 1)))
+        want = bool(log_every) or k == steps - 1 or record_every_loss
+        losses.append(net.train_step(data, models, rate, index=perm[pos:pos + batch], stream=stream,
+                                     want_loss=want))
+        pos += batch
+        if log_every and (k % log_every == 0 or k == steps - 1):
+            print(f"step {k:6d}  lr {rate:.2e}  loss {losses[-1]:.4e}", flush=True)
+    return losses
+
+
+# ------------------------------------------------------------------------------------------
+# the comparison: plain CGLS from zero against CGLS from the network's prediction
+
+def iterations_to_reach(residuals, target) -> int | None:
+    """First k with ||G x_k - d|| <= target, from a CGLS residual history (k = 0 is x0)."""
+    for k, r in enumerate(residuals):
+        if r <= target:
+            return k
+    return None
+
+
+def cgls_applies(iterations: int, warm: bool) -> int:
+    """G / G^T applies CGLS makes for k iterations: r0 = d - G x0 (skipped for x0 = 0),
+    s0 = G^T r0, and one G and one G^T per iteration."""
+    return (1 if warm else 0) + 1 + 2 * iterations
+
+
+def compare(op: "G.Operator", net: WarmStartNet, d, m_true=None, alpha: float = 1e-2, plain_iters: int = 50,
+            max_warm_iters: int | None = None, discrepancy: float | None = None):
+    """Plain CGLS from zero against CGLS from x0 = net(d) on the same Tikhonov system.
+
+    Plain CGLS stops at the first iteration whose misfit ||G x_k - d|| is at most `discrepancy`
+    (the discrepancy principle; without it, after `plain_iters` iterations); its misfit there is
+    the target.  The warm start stops at the first iteration that reaches the target.  Returns
+    a dict: the target, the iterations and G / G^T applies each run needs, the misfit of x0,
+    and (with m_true) the relative model errors of x0 and of both runs at their stopping
+    iterations."""
+    import torch
+
+    max_warm_iters = plain_iters if max_warm_iters is None else max_warm_iters
+    _, res_plain = op.cgls(d, alpha, plain_iters)
+    k_plain = plain_iters
+    if discrepancy is not None:
+        k = iterations_to_reach(res_plain, discrepancy)
+        k_plain = plain_iters if k is None else k
+    target = float(res_plain[k_plain])
+    x0 = net.forward(d.reshape(1, *d.shape))[0]
+    _, res_warm = op.cgls(d, alpha, max_warm_iters, x0=x0)
+    k_warm = iterations_to_reach(res_warm, target)
+    out = {
+        "alpha": alpha,
+        "target_misfit": target,
+        "plain_iterations": k_plain,
+        "plain_applies": cgls_applies(k_plain, False),
+        "warm_iterations": k_warm,
+        "warm_applies": None if k_warm is None else cgls_applies(k_warm, True),
+        "x0_misfit": float(res_warm[0]),
+        "data_norm": float(d.double().norm()),
+        "plain_residuals": [float(r) for r in res_plain],
+        "warm_residuals": [float(r) for r in res_warm],
+    }
+    if m_true is not None:
+        mt = m_true.double()
+        nrm = float(mt.norm())
+        x_plain, _ = op.cgls(d, alpha, k_plain)  # CGLS is deterministic: the same iterates again
+        out["x0_model_error"] = float((x0.double() - mt).norm()) / nrm
+        out["plain_model_error"] = float((x_plain.double() - mt).norm()) / nrm
+        if k_warm is not None:
+            x_warm, _ = op.cgls(d, alpha, k_warm, x0=x0)
+            out["warm_model_error"] = float((x_warm.double() - mt).norm()) / nrm
+    torch.cuda.synchronize()
+    return out

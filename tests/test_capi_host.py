@@ -1,7 +1,8 @@
 """The C ABI on the host (no GPU needed): the library builds and loads, exports
-every function include/gravmag.h declares, and its host-only logic (FFT length
-choice, parameter validation, no-device behaviour) is right."""
+every function the headers under include/ declare, and its host-only logic (FFT
+length choice, parameter validation, no-device behaviour) is right."""
 import ctypes
+import glob
 import os
 import re
 
@@ -20,17 +21,22 @@ def lib():
     return gravmag
 
 
-def _declared_functions():
-    txt = open(os.path.join(ROOT, "include", "gravmag.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return re.findall(r"^GM_API\s+[\w\s\*]*?\b(\w+)\s*\(", txt, flags=re.M)
+def _declared_functions(header=None):
+    names = []
+    for path in sorted(glob.glob(os.path.join(ROOT, "include", header or "*.h"))):
+        txt = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+        names += re.findall(r"^GM_API\s+[\w\s\*]*?\b(\w+)\s*\(", txt, flags=re.M)
+    return names
 
 
 def test_header_declares_the_boundary():
-    names = _declared_functions()
+    names = _declared_functions("gravmag.h")
     for required in ("grav_mag_setup", "grav_mag_setup_ex", "apply_forward", "apply_transpose",
-                     "grav_mag_destroy", "gm_status_string"):
+                     "grav_mag_destroy", "gm_status_string", "gm_cgls"):
         assert required in names
+    net = _declared_functions("gm_warmstart.h")
+    for required in ("gm_net_create", "gm_net_forward", "gm_net_train_step", "gm_net_get_params"):
+        assert required in net
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -101,3 +107,22 @@ def test_setup_without_a_device_fails_cleanly(lib):
     assert so.gm_last_status() == lib.GM_ENODEV
     assert so.apply_forward(None, None, None, None) == lib.GM_EINVAL
     assert so.grav_mag_destroy(None) == lib.GM_OK
+
+
+def test_network_rejects_bad_arguments_without_a_device(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1912_06976_gb300 import warmstart
+
+    so = warmstart._lib()
+    assert not so.gm_net_create(40, 16, 4, 0)  # grid not a multiple of 16
+    assert not so.gm_net_create(64, 8, 4, 0)   # depth other than 16
+    assert not so.gm_net_create(64, 16, 0, 0)  # empty batch
+    assert not so.gm_net_create(64, 16, 4, 0)  # valid, but no device
+    assert b"device" in so.gm_net_last_error()
+    assert so.gm_net_forward(None, None, None, 1, None) == lib.GM_EINVAL
+    assert so.gm_net_train_step(None, None, None, 1, None, 1, 0.0, None, None) == lib.GM_EINVAL
+    assert so.gm_net_num_params(None) == -1
+    assert so.gm_net_destroy(None) == lib.GM_OK

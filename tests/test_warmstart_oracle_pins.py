@@ -123,3 +123,35 @@ def test_adam_matches_scalar_rule():
     v = 0.999 * 0.001 * 0.04 + 0.001 * 0.01
     assert np.allclose(w2, w1 - 0.01 * (a / (1 - 0.81)) / (np.sqrt(v / (1 - 0.999 ** 2)) + 1e-8), rtol=0,
                        atol=1e-15)
+
+
+def test_data_term_gradient_matches_finite_differences():
+    """The loss with the data-consistency term, G a random dense matrix (S = 16)."""
+    S = 16
+    rng = np.random.default_rng(8)
+    p = rng.standard_normal(N.num_params()) * 0.05
+    d = rng.standard_normal((2, S, S))
+    m = rng.standard_normal((2, 16, S, S))
+    G = rng.standard_normal((S * S, 16 * S * S)) / 64.0
+    loss, g = N.loss_and_grad(p, d, m, 0.9, 1.2, G, 0.7)
+    assert abs(loss - N.loss(p, d, m, 0.9, 1.2, G, 0.7)) < 1e-14 * abs(loss)
+    assert loss > N.loss(p, d, m, 0.9, 1.2)  # the term is added, and positive
+    h = 1e-5
+    for k in range(3):
+        v = np.random.default_rng((k, 10)).standard_normal(p.size)
+        v /= np.linalg.norm(v)
+        fd = (N.loss(p + h * v, d, m, 0.9, 1.2, G, 0.7) - N.loss(p - h * v, d, m, 0.9, 1.2, G, 0.7)) / (2 * h)
+        assert abs(fd - g @ v) <= 1e-6 * max(abs(fd), np.linalg.norm(g) * 1e-3)
+
+
+def test_data_term_of_an_exact_model_is_zero():
+    """If net(d) reproduces a model whose data are d, the data term vanishes: a network whose last
+    layer is zero predicts its bias, so G applied to that constant model gives d exactly."""
+    S = 16
+    p = np.zeros(N.num_params())
+    p[-1] = 0.25  # bias of the output layer: f = 0.25 everywhere
+    G = np.random.default_rng(2).standard_normal((S * S, 16 * S * S))
+    mp = np.full(16 * S * S, 0.25 * 1.5)
+    d = (G @ mp).reshape(1, S, S)
+    base = N.loss(p, d, np.zeros((1, 16, S, S)), 1.0, 1.5)
+    assert abs(N.loss(p, d, np.zeros((1, 16, S, S)), 1.0, 1.5, G, 3.0) - base) < 1e-20 + 1e-12 * base
