@@ -335,3 +335,116 @@ def compare(op: "G.Operator", net: WarmStartNet, d, m_true=None, alpha: float = 
             out["warm_model_error"] = float((x_warm.double() - mt).norm()) / nrm
     torch.cuda.synchronize()
     return out
+
+
+def report(count: int = 20000, steps: int = 6000, batch: int = 32, lr: float = 1e-3, lam: float = 0.0,
+           tests: int = 32, alpha: float = 1e-2, noise: float = 0.01, seed: int = 0, max_iters: int = 60,
+           save: str | None = None, log_every: int = 500):
+    """Train on `count` seeded pairs of the 64 x 64 x 16 gravity grid and compare warm-started with
+    plain CGLS on `tests` held-out pairs (discrepancy principle with the known noise norm)."""
+    import time
+
+    import torch
+
+    w = W.WORKLOADS["grav64"]
+    op = G.Operator.from_workload(w, precision=G.F32)
+    t0 = time.perf_counter()
+    models_np = training_models(count + tests, seed=seed * 1000 + 1)
+    models = torch.as_tensor(models_np).cuda()
+    clean, noisy, noisy_np = make_data(op, models, noise, seed=seed * 1000 + 2)
+    gen_s = time.perf_counter() - t0
+    tr_m, tr_d = models[:count].contiguous(), noisy[:count].contiguous()
+    net = WarmStartNet(grid=w.sx, max_batch=batch, seed=seed * 1000 + 3)
+    net.set_scales(*fit_scales(models_np[:count], noisy_np[:count]))
+    if lam > 0:
+        net.set_data_term(op, lam)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = train(net, tr_m, tr_d, steps, batch, lr=lr, seed=seed, log_every=log_every, record_every_loss=False)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    if save:
+        net.save(save)
+    # inference and apply timing (CUDA events, after warm-up)
+    d1 = noisy[count:count + 1].contiguous()
+    for _ in range(3):
+        net.forward(d1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        net.forward(d1)
+    e1.record()
+    torch.cuda.synchronize()
+    infer_ms = e0.elapsed_time(e1) / 20
+    m1 = models[count].contiguous()
+    e0.record()
+    for _ in range(20):
+        op.forward(m1)
+        op.transpose(d1[0])
+    e1.record()
+    torch.cuda.synchronize()
+    apply_ms = e0.elapsed_time(e1) / 40
+    rows = []
+    for i in range(count, count + tests):
+        e = float((noisy[i].double() - clean[i].double()).norm())
+        r = compare(op, net, noisy[i].contiguous(), models[i], alpha=alpha, plain_iters=max_iters,
+                    max_warm_iters=max_iters, discrepancy=e)
+        r.pop("plain_residuals")
+        r.pop("warm_residuals")
+        r["noise_norm"] = e
+        rows.append(r)
+    reached = [r for r in rows if r["warm_applies"] is not None]
+
+    def mean(key, rs=rows):
+        vals = [r[key] for r in rs if r.get(key) is not None]
+        return float(np.mean(vals)) if vals else None
+
+    summary = {
+        "workload": "grav64: gravity 64x64 stations, 16 layers of 25 m cells, no padding",
+        "train_pairs": count, "steps": steps, "batch": batch, "lr": lr, "data_term_lambda": lam,
+        "noise": noise, "alpha": alpha, "tests": tests, "params": net.num_params,
+        "final_loss": losses[-1], "last_losses": net.last_losses(),
+        "generate_s": gen_s, "train_s": train_s, "train_step_ms": 1e3 * train_s / max(1, steps),
+        "net_forward_ms": infer_ms, "apply_ms": apply_ms,
+        "reached_target": len(reached),
+        "mean_plain_applies": mean("plain_applies"), "mean_warm_applies": mean("warm_applies", reached),
+        "mean_plain_applies_same_tests": mean("plain_applies", reached),
+        "fewer_applies": sum(1 for r in reached if r["warm_applies"] < r["plain_applies"]),
+        "more_applies": sum(1 for r in reached if r["warm_applies"] > r["plain_applies"]),
+        "mean_x0_misfit_rel": float(np.mean([r["x0_misfit"] / r["data_norm"] for r in rows])),
+        "mean_noise_rel": float(np.mean([r["noise_norm"] / r["data_norm"] for r in rows])),
+        "mean_x0_model_error": mean("x0_model_error"), "mean_plain_model_error": mean("plain_model_error"),
+        "mean_warm_model_error": mean("warm_model_error"),
+        "per_test": rows,
+    }
+    net.close()
+    op.close()
+    return summary
+
+
+def _main(argv=None):
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="train the warm-start network and compare with plain CGLS")
+    ap.add_argument("--count", type=int, default=20000)
+    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lam", type=float, default=0.0)
+    ap.add_argument("--tests", type=int, default=32)
+    ap.add_argument("--alpha", type=float, default=1e-2)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--save", default=None)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    s = report(a.count, a.steps, a.batch, a.lr, a.lam, a.tests, a.alpha, seed=a.seed, save=a.save)
+    brief = {k: v for k, v in s.items() if k != "per_test"}
+    print(json.dumps(brief), flush=True)
+    if a.out:
+        with open(a.out, "w") as f:
+            json.dump(s, f, indent=1)
+
+
+if __name__ == "__main__":
+    _main()
