@@ -25,9 +25,12 @@
  *   scaling  net(d) = out_scale * f(in_scale * d)
  * Parameters (1,858,849 for any S): for each layer in the order above its
  * weights w[co][ci][kd][kh][kw] followed by its biases b[co], one flat FP32
- * vector.  Convolutions read a BF16 copy of the weights and accumulate in
- * FP32; activations and gradients are FP32; Adam updates the FP32 master
- * weights and refreshes the BF16 copy.
+ * vector.  Every convolution of the forward pass and of the backward pass
+ * (data and weight gradients) is a tensor-core GEMM with BF16 operands and
+ * FP32 accumulation: BF16 copies of the weights, and activations / gradients
+ * (stored in FP32) rounded to BF16 as they are gathered; bias gradients are
+ * sums of the BF16-rounded output gradients.  Adam updates the FP32 master
+ * weights and refreshes the BF16 copies.
  *
  * Layouts: d[n][y][x] (batch n < batch, S x S, float), m[n][z][y][x] (16 x S x
  * S, float), both contiguous device buffers owned by the caller.  The handle
@@ -49,7 +52,7 @@ extern "C" {
 typedef struct gm_net *gm_net_handle;
 
 /* A network for S x S data (S a multiple of 16, 16 <= S <= 1024) and depth 16,
- * with buffers for up to max_batch examples.  Weights: He-uniform from a
+ * with buffers for up to max_batch examples (max_batch * 16 * S^2 <= 2^30).  Weights: He-uniform from a
  * counter-based generator (splitmix64 of seed and the parameter index);
  * biases 0.  NULL on failure (gm_net_last_error says why). */
 GM_API gm_net_handle gm_net_create(int grid, int depth, int max_batch, unsigned long long seed);
@@ -99,6 +102,25 @@ GM_API gm_status gm_net_get_params(gm_net_handle net, float *host, int64_t n, in
 GM_API gm_status gm_net_set_params(gm_net_handle net, const float *host, int64_t n, int which);
 GM_API gm_status gm_net_get_step(gm_net_handle net, int64_t *step);
 GM_API gm_status gm_net_set_step(gm_net_handle net, int64_t step);
+
+/* One convolution of the network's kind on its own, through the same
+ * tensor-core kernels (BF16 operands, FP32 accumulation): a 3-D
+ * cross-correlation with kernel KD x 3 x 3 (KD = 1 or 3), in-plane stride 1
+ * or 2, "same" zero padding (KD/2, 1, 1), on x[N][CI][ID][IH][IW]; the output
+ * is [N][CO][ID][OH][OW] with OH = (IH-1)/stride + 1, OW likewise.  CI and CO
+ * are powers of two (<= 4096).  w[CO][CI][KD][3][3] (device, FP32) is rounded
+ * to BF16 inside.
+ *   mode 0: out = conv(x) + b  (b may be NULL; g unused)
+ *   mode 1: out[N][CI][ID][IH][IW] = the data gradient for the output
+ *           gradient g[N][CO][ID][OH][OW]  (x unused)
+ *   mode 2: out[CO][CI][KD][3][3] = the weight gradient for x and g;
+ *           bias_grad[CO] (may be NULL) = SUM over n and positions of g
+ * Operands are rounded to BF16 as the network's kernels round them.  All
+ * pointers are device pointers owned by the caller; the call allocates
+ * scratch, runs on `stream` and synchronises it. */
+GM_API gm_status gm_conv3d(int mode, int N, int CI, int CO, int ID, int IH, int IW, int KD, int stride,
+                           const float *x, const float *g, const float *w, const float *b, float *out,
+                           float *bias_grad, void *stream);
 
 /* Kernels launched by the last forward / train-step call on this handle. */
 GM_API int gm_net_last_launch_count(gm_net_handle net);

@@ -21,7 +21,11 @@ convolved axis) and a bias.  Parameters are one flat vector: per layer, in
 the order above, w[co][ci][kd][kh][kw] then b[co].  The library convolves with
 BF16 weights; ``bf16_round`` gives the same weights here (round to nearest
 even of the FP32 value to 8 mantissa bits) so both sides use one set of
-numbers.  Gradients are torch.autograd in float64.
+numbers.  Gradients are torch.autograd in float64.  The library's tensor-core kernels also
+round the activations and gradients they multiply to BF16 (summing in FP32); with
+``bf16_operands=True`` the oracle rounds the same operands at the same places (its explicit
+backward formulas are pinned against autograd with the rounding switched off) and sums
+exactly, so only accumulation order and rare rounding-boundary cases differ.
 
 Pins (tests/test_warmstart_oracle_pins.py): the convolution step against a
 brute-force loop sum, the up-sampling and reshape against index formulas, the
@@ -88,6 +92,52 @@ def conv_weights_bf16(params) -> np.ndarray:
     return p
 
 
+def _round_bf16_tensor(t):
+    return torch.as_tensor(bf16_round(t.detach().numpy()))
+
+
+class _Bf16OperandConv(torch.autograd.Function):
+    """A convolution whose operands are BF16 values, summed exactly (float64): the forward
+    multiplies bf16(x) by the (already BF16) weights; the backward forms the data gradient from
+    bf16(g) and the weights, the weight gradient from bf16(x) and bf16(g), and the bias gradient
+    as the sum of bf16(g).  ``rounding=False`` leaves every operand as it is, which makes this
+    the plain convolution and its exact gradient."""
+
+    @staticmethod
+    def forward(ctx, x, w, b, stride, pad, rounding):
+        xr = _round_bf16_tensor(x) if rounding else x
+        ctx.save_for_backward(xr, w)
+        ctx.stride, ctx.pad, ctx.rounding = stride, pad, rounding
+        return F.conv3d(xr, w, b, stride=stride, padding=pad)
+
+    @staticmethod
+    def backward(ctx, g):
+        xr, w = ctx.saved_tensors
+        gr = _round_bf16_tensor(g) if ctx.rounding else g
+        dx = torch.nn.grad.conv3d_input(xr.shape, w, gr, stride=ctx.stride, padding=ctx.pad)
+        dw = torch.nn.grad.conv3d_weight(xr, w.shape, gr, stride=ctx.stride, padding=ctx.pad)
+        return dx, dw, gr.sum(dim=(0, 2, 3, 4)), None, None, None
+
+
+def conv_bf16(mode, w, x=None, g=None, b=None, stride=1, in_shape=None):
+    """One convolution with BF16-rounded operands summed exactly (the three products of
+    ``_Bf16OperandConv``): mode 0 conv(bf16(x), bf16(w)) + b; mode 1 the data gradient of shape
+    in_shape from bf16(g); mode 2 (weight gradient from bf16(x), bf16(g), sum of bf16(g))."""
+    wt = torch.as_tensor(bf16_round(np.asarray(w, dtype=np.float32)).reshape(np.shape(w)))
+    kd = wt.shape[2]
+    st, pad = (1, stride, stride), (kd // 2, 1, 1)
+    if mode == 0:
+        xr = torch.as_tensor(bf16_round(np.asarray(x, dtype=np.float32)).reshape(np.shape(x)))
+        bt = None if b is None else torch.as_tensor(np.asarray(b, dtype=np.float64))
+        return F.conv3d(xr, wt, bt, stride=st, padding=pad).numpy()
+    gr = torch.as_tensor(bf16_round(np.asarray(g, dtype=np.float32)).reshape(np.shape(g)))
+    if mode == 1:
+        return torch.nn.grad.conv3d_input(tuple(in_shape), wt, gr, stride=st, padding=pad).numpy()
+    xr = torch.as_tensor(bf16_round(np.asarray(x, dtype=np.float32)).reshape(np.shape(x)))
+    dw = torch.nn.grad.conv3d_weight(xr, tuple(wt.shape), gr, stride=st, padding=pad)
+    return dw.numpy(), gr.sum(dim=(0, 2, 3, 4)).numpy()
+
+
 def upsample(x, f):
     """Nearest up-sampling of N x C x D x H x W by integer factors f = (fz, fy, fx)."""
     for axis, k in zip((2, 3, 4), f):
@@ -96,24 +146,31 @@ def upsample(x, f):
     return x
 
 
-def f_scaled(layers, d, in_scale):
-    """f(in_scale d) for d of shape (N, S, S); returns (N, 16, S, S)."""
+def f_scaled(layers, d, in_scale, bf16_operands=False, explicit_backward=False):
+    """f(in_scale d) for d of shape (N, S, S); returns (N, 16, S, S).
+
+    bf16_operands: every convolution multiplies BF16-rounded operands (see _Bf16OperandConv),
+    as the tensor-core kernels do; explicit_backward without it runs the same explicit
+    gradient formulas with no rounding (used to pin them against autograd)."""
     x = (in_scale * d).unsqueeze(1).unsqueeze(1)  # N x 1 x 1 x S x S
     for idx, ((ci, co, kd, st, up, relu), (w, b)) in enumerate(zip(LAYERS, layers)):
         if idx == 5:  # the encoder's 512 x 1 x s x s output read as 128 x 4 x s x s
             n, c, _, h, ww = x.shape
             x = x.reshape(n, c // 4, 4, h, ww)
         x = upsample(x, up)
-        x = F.conv3d(x, w, b, stride=(1, st, st), padding=(kd // 2, 1, 1))
+        if bf16_operands or explicit_backward:
+            x = _Bf16OperandConv.apply(x, w, b, (1, st, st), (kd // 2, 1, 1), bf16_operands)
+        else:
+            x = F.conv3d(x, w, b, stride=(1, st, st), padding=(kd // 2, 1, 1))
         if relu:
             x = torch.relu(x)
     return x[:, 0]
 
 
-def forward(params, d, in_scale=1.0, out_scale=1.0) -> np.ndarray:
+def forward(params, d, in_scale=1.0, out_scale=1.0, bf16_operands=False) -> np.ndarray:
     """net(d) with the given parameters (used as they are: round them first for BF16 parity)."""
     with torch.no_grad():
-        y = f_scaled(unpack(params), torch.as_tensor(np.asarray(d, dtype=np.float64)), in_scale)
+        y = f_scaled(unpack(params), torch.as_tensor(np.asarray(d, dtype=np.float64)), in_scale, bf16_operands)
     return (out_scale * y).numpy()
 
 
@@ -126,9 +183,11 @@ def _data_term(y, d, in_scale, out_scale, G):
     return (r ** 2).mean()
 
 
-def loss_and_grad(params, d, m, in_scale=1.0, out_scale=1.0, G=None, lam=0.0):
+def loss_and_grad(params, d, m, in_scale=1.0, out_scale=1.0, G=None, lam=0.0, bf16_operands=False,
+                  explicit_backward=False):
     """(loss, gradient with respect to the flat parameter vector), float64.  With G and lam > 0
-    the loss adds lam times the data term of ``_data_term``."""
+    the loss adds lam times the data term of ``_data_term``; bf16_operands / explicit_backward as
+    in ``f_scaled``."""
     p = torch.tensor(np.asarray(params, dtype=np.float64), requires_grad=True)
     layers, off = [], 0
     for ci, co, kd, _, _, _ in LAYERS:
@@ -136,7 +195,7 @@ def loss_and_grad(params, d, m, in_scale=1.0, out_scale=1.0, G=None, lam=0.0):
         layers.append((p[off:off + nw].reshape(co, ci, kd, 3, 3), p[off + nw:off + nw + co]))
         off += nw + co
     dt = torch.as_tensor(np.asarray(d, dtype=np.float64))
-    y = f_scaled(layers, dt, in_scale)
+    y = f_scaled(layers, dt, in_scale, bf16_operands, explicit_backward)
     t = torch.as_tensor(np.asarray(m, dtype=np.float64)) / out_scale
     loss = ((y - t) ** 2).mean()
     if lam > 0:
@@ -145,10 +204,10 @@ def loss_and_grad(params, d, m, in_scale=1.0, out_scale=1.0, G=None, lam=0.0):
     return loss.item(), p.grad.numpy().copy()
 
 
-def loss(params, d, m, in_scale=1.0, out_scale=1.0, G=None, lam=0.0) -> float:
+def loss(params, d, m, in_scale=1.0, out_scale=1.0, G=None, lam=0.0, bf16_operands=False) -> float:
     with torch.no_grad():
         dt = torch.as_tensor(np.asarray(d, dtype=np.float64))
-        y = f_scaled(unpack(params), dt, in_scale)
+        y = f_scaled(unpack(params), dt, in_scale, bf16_operands)
         t = torch.as_tensor(np.asarray(m, dtype=np.float64)) / out_scale
         v = ((y - t) ** 2).mean()
         if lam > 0:

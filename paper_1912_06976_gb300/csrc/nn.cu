@@ -9,9 +9,11 @@
 //   decoder  D1 up (2,2,2), conv(3,3,3) 128 -> 64  ReLU     D2 up (2,2,2), conv 64 -> 32 ReLU
 //            D3 up (1,2,2), conv 32 -> 16 ReLU             D4 up (1,2,2), conv 16 -> 1 (linear)
 //   output   1 x 16 x S x S
-// Weights: FP32 master copies updated by Adam; the convolution kernels read a BF16 copy and
-// accumulate in FP32.  Every kernel here is plain CUDA-core code: direct convolutions with
-// weights broadcast across a block and several output channels per thread.
+// Weights: FP32 master copies updated by Adam, packed after every update into two BF16 GEMM
+// layouts.  Every convolution (forward, data gradient, weight gradient) is an implicit GEMM on
+// the tensor cores (tcgen05.mma, BF16 operands gathered on the fly from the FP32 activations and
+// gradients, FP32 accumulators in tensor memory); the element-wise steps (scaling, up-sampling,
+// ReLU masks, loss, Adam) are plain CUDA-core kernels.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -22,6 +24,7 @@
 #include <vector>
 
 #include "../../include/gm_warmstart.h"
+#include "gm_tcgen05.cuh"
 
 namespace gm {
 namespace nn {
@@ -37,220 +40,361 @@ struct ConvDims {
 
 __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
 
-constexpr int kChunk = 8;     // input (forward) or output (data gradient) channels staged per round
-constexpr int kMaxTaps = 27;  // 3 x 3 x 3
+// ------------------------------------------------------------------------------------------
+// Convolutions as implicit GEMMs on the tensor cores (tcgen05, BF16 operands, FP32 accumulators
+// in tensor memory).  One CTA of 256 threads computes a 128 x BN tile of D = A B^T over K in
+// blocks of 64, two shared-memory stages deep: all threads gather the next block of A and B
+// (FP32 activations / gradients rounded to BF16, packed BF16 weights) while the tensor cores
+// multiply the previous one; thread 0 issues the MMAs and commits each stage to an mbarrier.
+//
+//   FWD    rows = output positions (n, o)       cols = co   K = (tap, ci)  A = x, B = packed w
+//          out[n][co][o] = b[co] + D, ReLU optional; x may be up-sampled on the fly (nearest,
+//          factors 1 or 2: the gather reads the stored tensor at coordinate >> factor)
+//   DGRAD  rows = input positions (n, i)        cols = ci   K = (tap, co)  A = g, B = packed w^T
+//          din[n][ci][i] = D   (g at o = (i + p - tap) / s where that is an integer in range)
+//   WGRAD  rows = (tap, ci), plus a row of ones  cols = co   K = positions of one chunk
+//          A = x shifted by the tap, B = g;  partial dW[co][ci][tap] and, from the ones row,
+//          partial db[co] of the chunk
+// FWD and DGRAD launches with fewer tiles than SMs split K over gridDim.z; each CTA then writes
+// its raw FP32 tile to part[z][col][row] and k_splitk_finish sums the parts in a fixed order.
+enum ConvMode { FWD = 0, DGRAD = 1, WGRAD = 2 };
 
-// Stage w[co0 + t][ci][tap] (forward, TRANS = false) or w[co][ci0 + t][tap] (data gradient,
-// TRANS = true) for the kChunk channels c0.. of the summed axis into smem[c][tap][t] as float.
-template <int CT, bool TRANS>
-__device__ __forceinline__ void stage_weights(float *sm, const __nv_bfloat16 *__restrict__ w, const ConvDims &d,
-                                              int fixed0, int c0, int K) {
-    const int n = kChunk * K * CT;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int t = e % CT, tap = (e / CT) % K, c = e / (CT * K);
-        const int sc = c0 + c, fc = fixed0 + t;  // summed channel, fixed channel
-        float v = 0.f;
-        if (!TRANS) {
-            if (sc < d.CI && fc < d.CO) v = bf(w[((size_t)fc * d.CI + sc) * K + tap]);
-        } else {
-            if (sc < d.CO && fc < d.CI) v = bf(w[((size_t)sc * d.CI + fc) * K + tap]);
-        }
-        sm[e] = v;
-    }
+struct ConvGemm {
+    ConvDims d;
+    int M;       // GEMM rows
+    int ncols;   // GEMM columns
+    int kreal;   // FWD / DGRAD: taps * (channels summed); WGRAD: positions N * osz
+    int kpitch;  // row length of the packed weights (multiple of 64), FWD / DGRAD
+    int lg;      // log2 of the channel count that K (FWD / DGRAD) or the rows (WGRAD) run over fastest
+    int chunk;   // WGRAD: positions per CTA (multiple of 64)
+    int taps;
+    int relu;
+    int ksplit, kbper;  // FWD / DGRAD: K blocks split over gridDim.z CTAs of kbper blocks each
+    int us[3];          // log2 of the nearest up-sampling (z, y, x) folded into the gathers of x
+    int LD, LH, LW;     // x before up-sampling (the stored tensor); (ID, IH, IW) = (LD, LH, LW) << us
+    long wait_limit;
+};
+
+constexpr int kTcThreads = 256;
+constexpr int kTcBK = 64;
+constexpr int kTileA = 128 * kTcBK * 2;  // bytes of one A stage
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-// out[n][co][o] = b[co] + SUM_ci SUM_taps w[co][ci][tap] in[n][ci][o*s + tap - p]; optional ReLU.
-// Block: blockDim.x output positions of one example, CT output channels per thread.
-template <int CT>
-__global__ void k_conv_fwd(const float *__restrict__ in, const __nv_bfloat16 *__restrict__ w,
-                           const float *__restrict__ b, float *__restrict__ out, ConvDims d, int relu) {
-    __shared__ __align__(16) float sw[kChunk * kMaxTaps * CT];
-    const int osz = d.OD * d.OH * d.OW;
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    const int co0 = blockIdx.y * CT;
-    const int n = blockIdx.z;
-    const bool active = o < osz;
-    const int oo = active ? o : 0;
-    const int ox = oo % d.OW, oy = (oo / d.OW) % d.OH, oz = oo / (d.OW * d.OH);
-    const int K = d.KD * d.KH * d.KW;
-    float acc[CT];
-#pragma unroll
-    for (int t = 0; t < CT; ++t) acc[t] = (co0 + t < d.CO) ? b[co0 + t] : 0.f;
-    const size_t isz = (size_t)d.ID * d.IH * d.IW;
-    const float *inn = in + (size_t)n * d.CI * isz;
-    for (int c0 = 0; c0 < d.CI; c0 += kChunk) {
-        __syncthreads();
-        stage_weights<CT, false>(sw, w, d, co0, c0, K);
-        __syncthreads();
-        if (!active) continue;
-        const int cn = min(kChunk, d.CI - c0);
-        for (int c = 0; c < cn; ++c) {
-            const float *inc = inn + (size_t)(c0 + c) * isz;
-            const float *swc = sw + c * K * CT;
-            for (int kz = 0; kz < d.KD; ++kz) {
-                const int iz = oz * d.SD + kz - d.PD;
-                if (iz < 0 || iz >= d.ID) continue;
-                for (int ky = 0; ky < d.KH; ++ky) {
-                    const int iy = oy * d.SH + ky - d.PH;
-                    if (iy < 0 || iy >= d.IH) continue;
-                    const float *row = inc + ((size_t)iz * d.IH + iy) * d.IW;
-                    const float *wt = swc + ((kz * d.KH + ky) * d.KW) * CT;
-                    for (int kx = 0; kx < d.KW; ++kx) {
-                        const int ix = ox * d.SW + kx - d.PW;
-                        if (ix < 0 || ix >= d.IW) continue;
-                        const float x = row[ix];
-#pragma unroll
-                        for (int t = 0; t < CT; ++t) acc[t] = fmaf(wt[kx * CT + t], x, acc[t]);
-                    }
-                }
-            }
-        }
+// q = t / s for s in {1, 2}; false unless t >= 0, s divides t and q < n
+__device__ __forceinline__ bool exact_div(int t, int s, int n, int &q) {
+    if (t < 0) return false;
+    if (s == 2) {
+        if (t & 1) return false;
+        t >>= 1;
     }
-    if (!active) return;
-#pragma unroll
-    for (int t = 0; t < CT; ++t)
-        if (co0 + t < d.CO) {
-            float v = acc[t];
-            if (relu) v = fmaxf(v, 0.f);
-            out[((size_t)n * d.CO + co0 + t) * osz + o] = v;
-        }
+    q = t;
+    return t < n;
 }
 
-// din[n][ci][i] = SUM_co SUM_taps w[co][ci][tap] g[n][co][(i + p - tap) / s]  (exact division only)
-template <int CT>
-__global__ void k_conv_bwd_data(const float *__restrict__ g, const __nv_bfloat16 *__restrict__ w,
-                                float *__restrict__ din, ConvDims d) {
-    __shared__ __align__(16) float sw[kChunk * kMaxTaps * CT];
-    const int isz = d.ID * d.IH * d.IW;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int ci0 = blockIdx.y * CT;
-    const int n = blockIdx.z;
-    const bool active = i < isz;
-    const int ii = active ? i : 0;
-    const int ix = ii % d.IW, iy = (ii / d.IW) % d.IH, iz = ii / (d.IW * d.IH);
-    const int K = d.KD * d.KH * d.KW;
-    const size_t osz = (size_t)d.OD * d.OH * d.OW;
-    float acc[CT];
-#pragma unroll
-    for (int t = 0; t < CT; ++t) acc[t] = 0.f;
-    const float *gn = g + (size_t)n * d.CO * osz;
-    for (int c0 = 0; c0 < d.CO; c0 += kChunk) {
-        __syncthreads();
-        stage_weights<CT, true>(sw, w, d, ci0, c0, K);
-        __syncthreads();
-        if (!active) continue;
-        const int cn = min(kChunk, d.CO - c0);
-        for (int c = 0; c < cn; ++c) {
-            const float *gc = gn + (size_t)(c0 + c) * osz;
-            const float *swc = sw + c * K * CT;
-            for (int kz = 0; kz < d.KD; ++kz) {
-                const int tz = iz + d.PD - kz;
-                if (tz < 0 || tz % d.SD) continue;
-                const int oz = tz / d.SD;
-                if (oz >= d.OD) continue;
-                for (int ky = 0; ky < d.KH; ++ky) {
-                    const int ty = iy + d.PH - ky;
-                    if (ty < 0 || ty % d.SH) continue;
-                    const int oy = ty / d.SH;
-                    if (oy >= d.OH) continue;
-                    const float *row = gc + ((size_t)oz * d.OH + oy) * d.OW;
-                    const float *wt = swc + ((kz * d.KH + ky) * d.KW) * CT;
-                    for (int kx = 0; kx < d.KW; ++kx) {
-                        const int tx = ix + d.PW - kx;
-                        if (tx < 0 || tx % d.SW) continue;
-                        const int ox = tx / d.SW;
-                        if (ox >= d.OW) continue;
-                        const float gv = row[ox];
-#pragma unroll
-                        for (int t = 0; t < CT; ++t) acc[t] = fmaf(wt[kx * CT + t], gv, acc[t]);
-                    }
-                }
-            }
-        }
-    }
-    if (!active) return;
-#pragma unroll
-    for (int t = 0; t < CT; ++t)
-        if (ci0 + t < d.CI) din[((size_t)n * d.CI + ci0 + t) * isz + i] = acc[t];
+__device__ __forceinline__ void decode_tap(int tap, int &kz, int &ky, int &kx) {
+    kz = tap / 9;
+    const int r = tap - 9 * kz;
+    ky = r / 3;
+    kx = r - 3 * ky;
 }
 
-
-// Partial weight and bias gradients over one chunk of the (example, output position) pairs:
-//   dwp[chunk][co][ci][kz][ky][kx] = SUM g[n][co][o] in[n][ci][o*s + (kz,ky,kx) - p]
-//   dbp[chunk][co]                 = SUM g[n][co][o]                 (blocks with ci = kz = 0)
-// Block (co tile of COT channels, ci, kz) x chunk; each thread keeps COT x 9 (ky, kx) sums in
-// registers over its positions (per position: COT gradient loads, 9 input loads, 9 COT FMAs),
-// then the block reduces them with warp shuffles and shared memory.
-template <int COT>
-__global__ void __launch_bounds__(256) k_conv_wgrad(const float *__restrict__ g, const float *__restrict__ in,
-                                                    float *__restrict__ dwp, float *__restrict__ dbp, ConvDims d,
-                                                    int chunk) {
-    int bx = blockIdx.x;
-    const int kz = bx % d.KD;
-    bx /= d.KD;
-    const int ci = bx % d.CI;
-    const int co0 = (bx / d.CI) * COT;
-    const int osz = d.OD * d.OH * d.OW;
-    const long long total = (long long)d.N * osz;
-    const long long beg = (long long)blockIdx.y * chunk;
-    const long long end = min(total, beg + chunk);
-    const size_t isz = (size_t)d.ID * d.IH * d.IW;
-    float acc[COT][9], accb[COT];
-#pragma unroll
-    for (int t = 0; t < COT; ++t) {
-        accb[t] = 0.f;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) acc[t][q] = 0.f;
+template <int MODE>
+__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict__ act, const float *__restrict__ grad,
+                                                        const __nv_bfloat16 *__restrict__ wpk,
+                                                        const float *__restrict__ bias, float *__restrict__ out,
+                                                        float *__restrict__ out2, ConvGemm p, int bn,
+                                                        int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint32_t tmem_base;
+    __shared__ __align__(8) uint64_t bars[2];
+    const ConvDims &d = p.d;
+    const int t = threadIdx.x;
+    const int r = t & 127;  // the GEMM row this thread gathers and, in the epilogue, stores
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * bn;
+    const int stage_bytes = kTileA + bn * 128;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)bn) cols <<= 1;
+    if (t < 32) gm::tc::tmem_alloc(&tmem_base, cols);
+    if (t == 0) {
+        gm::tc::mbar_init(&bars[0], 1);
+        gm::tc::mbar_init(&bars[1], 1);
     }
-    for (long long e = beg + threadIdx.x; e < end; e += blockDim.x) {
-        const int n = (int)(e / osz), o = (int)(e - (long long)n * osz);
-        const int ox = o % d.OW, oy = (o / d.OW) % d.OH, oz = o / (d.OW * d.OH);
-        float gv[COT];
-#pragma unroll
-        for (int t = 0; t < COT; ++t) {
-            gv[t] = (co0 + t < d.CO) ? g[((size_t)n * d.CO + co0 + t) * osz + o] : 0.f;
-            accb[t] += gv[t];
-        }
-        const int iz = oz * d.SD + kz - d.PD;
-        if (iz < 0 || iz >= d.ID) continue;
-        const float *plane = in + ((size_t)n * d.CI + ci) * isz + (size_t)iz * d.IH * d.IW;
-#pragma unroll
-        for (int ky = 0; ky < 3; ++ky) {
-            const int iy = oy * d.SH + ky - d.PH;
-            const bool vy = iy >= 0 && iy < d.IH;
-#pragma unroll
-            for (int kx = 0; kx < 3; ++kx) {
-                const int ix = ox * d.SW + kx - d.PW;
-                const float x = (vy && ix >= 0 && ix < d.IW) ? plane[(size_t)iy * d.IW + ix] : 0.f;
-#pragma unroll
-                for (int t = 0; t < COT; ++t) acc[t][ky * 3 + kx] = fmaf(gv[t], x, acc[t][ky * 3 + kx]);
-            }
-        }
-    }
-    // block reduction of the COT * 10 sums
-    constexpr int NV = COT * 10;
-    __shared__ float red[8][NV];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-#pragma unroll
-    for (int t = 0; t < COT; ++t) {
-#pragma unroll
-        for (int q = 0; q < 10; ++q) {
-            float v = q < 9 ? acc[t][q] : accb[t];
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if (lane == 0) red[warp][t * 10 + q] = v;
-        }
-    }
+    gm::tc::fence_before_sync();
     __syncthreads();
-    for (int i = threadIdx.x; i < NV; i += blockDim.x) {
-        float v = 0.f;
-        for (int w = 0; w < nwarp; ++w) v += red[w][i];
-        const int t = i / 10, q = i % 10, co = co0 + t;
-        if (co >= d.CO) continue;
-        if (q < 9) {
-            dwp[(size_t)blockIdx.y * d.CO * d.CI * d.KD * 9 + (((size_t)co * d.CI + ci) * d.KD + kz) * 9 + q] = v;
-        } else if (ci == 0 && kz == 0) {
-            dbp[(size_t)blockIdx.y * d.CO + co] = v;
+    gm::tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    const int osz = d.OD * d.OH * d.OW, isz = d.ID * d.IH * d.IW;
+    // FWD / DGRAD: this thread's row is a position
+    int rn = -1, rz = 0, ry = 0, rx = 0, ro = 0;
+    if (MODE != WGRAD) {
+        const int m = m0 + r;
+        if (m < p.M) {
+            const int per = MODE == FWD ? osz : isz;
+            const int W = MODE == FWD ? d.OW : d.IW, H = MODE == FWD ? d.OH : d.IH;
+            rn = m / per;
+            ro = m - rn * per;
+            rx = ro % W;
+            ry = (ro / W) % H;
+            rz = ro / (W * H);
         }
+    }
+    const int q0 = MODE == WGRAD ? blockIdx.z * p.chunk : 0;
+    const int kb0 = MODE == WGRAD ? 0 : blockIdx.z * p.kbper;
+    const int nkb = MODE == WGRAD ? p.chunk / kTcBK : min(p.kbper, p.kpitch / kTcBK - kb0);
+    const int cmask = (1 << p.lg) - 1;
+    const size_t lsz = (size_t)p.LD * p.LH * p.LW;  // stored (not up-sampled) x per channel
+    const uint32_t idesc = gm::tc::instr_desc_bf16(128, bn);
+    bool ok = true;
+
+    for (int it = 0; it < nkb; ++it) {
+        const int kb = kb0 + it;
+        const int s = it & 1;
+        unsigned char *sa = smem + s * stage_bytes;
+        unsigned char *sb = sa + kTileA;
+        if (it >= 2) {  // the MMAs of block it - 2 read this stage
+            const bool got = gm::tc::mbar_wait(&bars[s], ((it - 2) >> 1) & 1, p.wait_limit);
+            if (__syncthreads_or(!got)) {
+                ok = false;
+                break;
+            }
+        }
+        // ---- A: 128 rows x 8 core columns
+        if (MODE == FWD || MODE == DGRAD) {
+            const int C = MODE == FWD ? d.CI : d.CO;  // channels K runs over
+            const float *src = MODE == FWD ? act : grad;
+            const size_t cstride = MODE == FWD ? lsz : (size_t)osz;
+            const float *base = src + (size_t)(rn < 0 ? 0 : rn) * C * cstride;
+            for (int kc = (t >> 7) * 4; kc < (t >> 7) * 4 + 4; ++kc) {
+                const int k0 = kb * kTcBK + kc * 8;
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = 0.f;
+                if (rn >= 0 && k0 < p.kreal) {
+                    if (C >= 8) {  // the 8 elements share one tap
+                        const int tap = k0 >> p.lg, c0 = k0 & cmask;
+                        int kz, ky, kx;
+                        decode_tap(tap, kz, ky, kx);
+                        int a, b, c;
+                        bool in;
+                        if (MODE == FWD) {
+                            a = rz * d.SD + kz - d.PD;
+                            b = ry * d.SH + ky - d.PH;
+                            c = rx * d.SW + kx - d.PW;
+                            in = a >= 0 && a < d.ID && b >= 0 && b < d.IH && c >= 0 && c < d.IW;
+                        } else {
+                            in = exact_div(rz + d.PD - kz, d.SD, d.OD, a) && exact_div(ry + d.PH - ky, d.SH, d.OH, b) &&
+                                 exact_div(rx + d.PW - kx, d.SW, d.OW, c);
+                        }
+                        if (in) {
+                            if (MODE == FWD) {
+                                a >>= p.us[0];
+                                b >>= p.us[1];
+                                c >>= p.us[2];
+                            }
+                            const int H = MODE == FWD ? p.LH : d.OH, W = MODE == FWD ? p.LW : d.OW;
+                            const float *q = base + (size_t)c0 * cstride + ((size_t)a * H + b) * W + c;
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) v[e] = q[(size_t)e * cstride];
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int k = k0 + e;
+                            if (k >= p.kreal) break;
+                            const int tap = k >> p.lg, ch = k & cmask;
+                            int kz, ky, kx;
+                            decode_tap(tap, kz, ky, kx);
+                            int a, b, c;
+                            bool in;
+                            if (MODE == FWD) {
+                                a = rz * d.SD + kz - d.PD;
+                                b = ry * d.SH + ky - d.PH;
+                                c = rx * d.SW + kx - d.PW;
+                                in = a >= 0 && a < d.ID && b >= 0 && b < d.IH && c >= 0 && c < d.IW;
+                            } else {
+                                in = exact_div(rz + d.PD - kz, d.SD, d.OD, a) &&
+                                     exact_div(ry + d.PH - ky, d.SH, d.OH, b) && exact_div(rx + d.PW - kx, d.SW, d.OW, c);
+                            }
+                            if (in) {
+                                if (MODE == FWD) {
+                                    a >>= p.us[0];
+                                    b >>= p.us[1];
+                                    c >>= p.us[2];
+                                }
+                                const int H = MODE == FWD ? p.LH : d.OH, W = MODE == FWD ? p.LW : d.OW;
+                                v[e] = base[(size_t)ch * cstride + ((size_t)a * H + b) * W + c];
+                            }
+                        }
+                    }
+                }
+                const uint4 pk = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                                            pack_bf16x2(v[6], v[7]));
+                *reinterpret_cast<uint4 *>(sa + gm::tc::tile_offset(r, kc)) = pk;
+            }
+        } else {
+            // WGRAD: warp w fills core column w (positions 8w..8w+7 of the block) of A and B;
+            // lane (row r = lane & 7, pair j = lane >> 3) holds positions 8w + 2j and 8w + 2j + 1,
+            // so one 4-byte store per lane fills one 8 x 8 core matrix
+            const int warp = t >> 5, lane = t & 31, rr = lane & 7, j = lane >> 3;
+            int pn[2], pz[2], py[2], px[2], po[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int q = q0 + kb * kTcBK + warp * 8 + 2 * j + e;
+                pn[e] = -1;
+                pz[e] = py[e] = px[e] = po[e] = 0;
+                if (q < p.kreal) {
+                    pn[e] = q / osz;
+                    po[e] = q - pn[e] * osz;
+                    px[e] = po[e] % d.OW;
+                    py[e] = (po[e] / d.OW) % d.OH;
+                    pz[e] = po[e] / (d.OW * d.OH);
+                }
+            }
+            const int nrow = p.taps << p.lg;
+            for (int grp = 0; grp < 16; ++grp) {  // A rows (tap, ci), then the ones row
+                const int row = grp * 8 + rr, kk = m0 + row;
+                float v[2] = {0.f, 0.f};
+                if (kk < nrow) {
+                    const int tap = kk >> p.lg, ci = kk & cmask;
+                    int kz, ky, kx;
+                    decode_tap(tap, kz, ky, kx);
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        if (pn[e] < 0) continue;
+                        const int a = pz[e] * d.SD + kz - d.PD, b = py[e] * d.SH + ky - d.PH,
+                                  c = px[e] * d.SW + kx - d.PW;
+                        if (a >= 0 && a < d.ID && b >= 0 && b < d.IH && c >= 0 && c < d.IW)
+                            v[e] = act[((size_t)pn[e] * d.CI + ci) * lsz +
+                                       ((size_t)(a >> p.us[0]) * p.LH + (b >> p.us[1])) * p.LW + (c >> p.us[2])];
+                    }
+                } else if (kk == nrow) {
+                    v[0] = pn[0] >= 0 ? 1.f : 0.f;
+                    v[1] = pn[1] >= 0 ? 1.f : 0.f;
+                }
+                *reinterpret_cast<uint32_t *>(sa + gm::tc::tile_offset(row, warp) + 4 * j) = pack_bf16x2(v[0], v[1]);
+            }
+            for (int grp = 0; grp < (bn >> 3); ++grp) {  // B rows co
+                const int row = grp * 8 + rr, col = n0 + row;
+                float v[2] = {0.f, 0.f};
+                if (col < p.ncols) {
+#pragma unroll
+                    for (int e = 0; e < 2; ++e)
+                        if (pn[e] >= 0) v[e] = grad[((size_t)pn[e] * d.CO + col) * osz + po[e]];
+                }
+                *reinterpret_cast<uint32_t *>(sb + gm::tc::tile_offset(row, warp) + 4 * j) = pack_bf16x2(v[0], v[1]);
+            }
+        }
+        // ---- B of FWD / DGRAD: bn rows x 8 core columns of packed weights
+        if (MODE != WGRAD) {
+            for (int pr = t; pr < bn * 8; pr += kTcThreads) {
+                const int kc = pr & 7, row = pr >> 3, col = n0 + row;
+                uint4 pk = make_uint4(0, 0, 0, 0);
+                if (col < p.ncols)
+                    pk = *reinterpret_cast<const uint4 *>(wpk + (size_t)col * p.kpitch + kb * kTcBK + kc * 8);
+                *reinterpret_cast<uint4 *>(sb + gm::tc::tile_offset(row, kc)) = pk;
+            }
+        }
+        gm::tc::fence_smem_to_async();
+        __syncthreads();
+        if (t == 0) {
+            gm::tc::fence_after_sync();
+            const uint32_t a0 = gm::tc::smem_u32(sa), b0 = gm::tc::smem_u32(sb);
+#pragma unroll
+            for (int j = 0; j < kTcBK / 16; ++j)
+                gm::tc::mma_bf16(tmem, gm::tc::smem_desc(a0 + j * 256), gm::tc::smem_desc(b0 + j * 256), idesc,
+                                 it > 0 || j > 0);
+            gm::tc::commit(&bars[s]);
+        }
+    }
+    if (ok) {
+        const bool got = gm::tc::mbar_wait(&bars[(nkb - 1) & 1], ((nkb - 1) >> 1) & 1, p.wait_limit);
+        if (__syncthreads_or(!got)) ok = false;
+    }
+    if (!ok) {
+        if (t == 0) atomicExch(err, 1);
+    } else {
+        gm::tc::fence_after_sync();
+        const int warp = t >> 5;
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        const int half = bn >> 1, c_begin = (warp >> 2) * half;
+        const int nrow = p.taps << p.lg;
+        for (int cc = c_begin; cc < c_begin + half; cc += 8) {
+            float v[8];
+            gm::tc::tmem_ld8(tmem + lane_base + cc, v);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int col = n0 + cc + e;
+                if (col >= p.ncols) continue;
+                if (MODE != WGRAD && p.ksplit > 1) {
+                    if (rn < 0) continue;
+                    out2[((size_t)blockIdx.z * p.ncols + col) * p.M + m0 + r] = v[e];
+                } else if (MODE == FWD) {
+                    if (rn < 0) continue;
+                    float x = v[e] + bias[col];
+                    if (p.relu) x = fmaxf(x, 0.f);
+                    out[((size_t)rn * d.CO + col) * osz + ro] = x;
+                } else if (MODE == DGRAD) {
+                    if (rn < 0) continue;
+                    out[((size_t)rn * d.CI + col) * isz + ro] = v[e];
+                } else {
+                    const int kk = m0 + r;
+                    if (kk < nrow) {
+                        const int tap = kk >> p.lg, ci = kk & cmask;
+                        out[(size_t)blockIdx.z * d.CO * d.CI * p.taps + ((size_t)col * d.CI + ci) * p.taps + tap] =
+                            v[e];
+                    } else if (kk == nrow) {
+                        out2[(size_t)blockIdx.z * d.CO + col] = v[e];
+                    }
+                }
+            }
+        }
+    }
+    gm::tc::fence_before_sync();
+    __syncthreads();
+    if (t < 32) gm::tc::tmem_free(tmem, cols);
+}
+
+// out[n][c][o] = SUM_z part[z][c][m] (z < ksplit, in order) [+ bias[c], ReLU], m = n * per + o
+__global__ void k_splitk_finish(const float *__restrict__ part, int ksplit, int M, int ncols, int per,
+                                const float *__restrict__ bias, int relu, float *__restrict__ out) {
+    const size_t total = (size_t)M * ncols;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i / M), m = (int)(i - (size_t)c * M);
+        float v = 0.f;
+        for (int z = 0; z < ksplit; ++z) v += part[((size_t)z * ncols + c) * M + m];
+        if (bias) v += bias[c];
+        if (relu) v = fmaxf(v, 0.f);
+        const int n = m / per, o = m - n * per;
+        out[((size_t)n * ncols + c) * per + o] = v;
+    }
+}
+
+// Packed BF16 weights of every layer: wf[co][tap * CI + ci] (FWD) and wd[ci][tap * CO + co]
+// (DGRAD), rows padded with zeros to a multiple of 64 elements.
+struct PackTable {
+    int nl;
+    int CI[12], CO[12], taps[12], kf[12], kd[12];
+    long long w_off[12], f_off[12], d_off[12], cum[13];
+};
+
+__global__ void k_pack_weights(const float *__restrict__ w, __nv_bfloat16 *__restrict__ wf,
+                               __nv_bfloat16 *__restrict__ wd, PackTable tb) {
+    const long long total = tb.cum[tb.nl];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (l + 1 < tb.nl && i >= tb.cum[l + 1]) ++l;
+        const long long loc = i - tb.cum[l];
+        const int taps = tb.taps[l], CI = tb.CI[l], CO = tb.CO[l];
+        const int tap = (int)(loc % taps), ci = (int)((loc / taps) % CI), co = (int)(loc / ((long long)taps * CI));
+        const __nv_bfloat16 v = __float2bfloat16(w[tb.w_off[l] + loc]);
+        wf[tb.f_off[l] + (long long)co * tb.kf[l] + (long long)tap * CI + ci] = v;
+        wd[tb.d_off[l] + (long long)ci * tb.kd[l] + (long long)tap * CO + co] = v;
     }
 }
 
@@ -263,29 +407,21 @@ __global__ void k_sum_chunks(const float *__restrict__ part, float *__restrict__
     }
 }
 
-// nearest up-sampling by (fz, fy, fx): out[n][c][z][y][x] = in[n][c][z/fz][y/fy][x/fx]
-__global__ void k_upsample(const float *__restrict__ in, float *__restrict__ out, int NC, int D, int H, int W, int fz,
-                           int fy, int fx) {
-    const size_t OD = (size_t)D * fz, OH = (size_t)H * fy, OW = (size_t)W * fx;
-    const size_t tot = (size_t)NC * OD * OH * OW;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t x = i % OW, y = (i / OW) % OH, z = (i / (OW * OH)) % OD, c = i / (OW * OH * OD);
-        out[i] = in[((c * D + z / fz) * H + y / fy) * W + x / fx];
-    }
-}
-
-// adjoint of k_upsample: in[n][c][z][y][x] = SUM of out over its (fz, fy, fx) block
+// adjoint of nearest up-sampling: gin[c][z][y][x] = SUM of gout over its (fz, fy, fx) block
+// (sizes below 2^31, which gm_net_create guarantees)
 __global__ void k_upsample_bwd(const float *__restrict__ gout, float *__restrict__ gin, int NC, int D, int H, int W,
                                int fz, int fy, int fx) {
-    const size_t tot = (size_t)NC * D * H * W;
-    const size_t OH = (size_t)H * fy, OW = (size_t)W * fx, OD = (size_t)D * fz;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t x = i % W, y = (i / W) % H, z = (i / ((size_t)W * H)) % D, c = i / ((size_t)W * H * D);
+    const int tot = NC * D * H * W;
+    const int OH = H * fy, OW = W * fx, OD = D * fz;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += gridDim.x * blockDim.x) {
+        const int x = i % W, y = (i / W) % H, zc = i / (W * H);
+        const int z = zc % D, c = zc / D;
         float s = 0.f;
         for (int a = 0; a < fz; ++a)
-            for (int bq = 0; bq < fy; ++bq)
-                for (int e = 0; e < fx; ++e)
-                    s += gout[((c * OD + z * fz + a) * OH + y * fy + bq) * OW + x * fx + e];
+            for (int b = 0; b < fy; ++b) {
+                const float *row = gout + ((size_t)(c * OD + z * fz + a) * OH + y * fy + b) * OW + x * fx;
+                for (int e = 0; e < fx; ++e) s += row[e];
+            }
         gin[i] = s;
     }
 }
@@ -325,9 +461,9 @@ __global__ void k_loss_final(const float *__restrict__ part, int nb, float *__re
     }
 }
 
-// Adam with bias correction; w (FP32 master) and its BF16 copy
+// Adam with bias correction on the FP32 master weights (the packed BF16 copies are rebuilt after)
 __global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m1,
-                       float *__restrict__ m2, __nv_bfloat16 *__restrict__ wb, size_t n, float lr, float b1, float b2,
+                       float *__restrict__ m2, size_t n, float lr, float b1, float b2,
                        float eps, float c1, float c2) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -337,7 +473,6 @@ __global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float
         m2[i] = v;
         const float wi = w[i] - lr * (a / c1) / (sqrtf(v / c2) + eps);
         w[i] = wi;
-        if (wb) wb[i] = __float2bfloat16(wi);
     }
 }
 
@@ -367,10 +502,6 @@ __global__ void k_axpy(float *__restrict__ y, const float *__restrict__ x, float
         y[i] = fmaf(a, x[i], y[i]);
 }
 
-__global__ void k_to_bf16(const float *__restrict__ w, __nv_bfloat16 *__restrict__ wb, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        wb[i] = __float2bfloat16(w[i]);
-}
 
 __global__ void k_scale(const float *__restrict__ x, float *__restrict__ y, size_t n, float a) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -401,6 +532,8 @@ struct Layer {
     int in_d, in_h, in_w;  // input before up-sampling
     bool relu;
     size_t w_off, b_off, nw;
+    int taps, kf, kd;        // taps; packed row lengths of the FWD and DGRAD weight layouts
+    size_t f_off, d_off;     // offsets of the packed layouts
     bool upsampled() const { return up[0] * up[1] * up[2] > 1; }
     size_t in_low(int N) const { return (size_t)N * d.CI * in_d * in_h * in_w; }
     size_t in_up(int N) const { return (size_t)N * d.CI * d.ID * d.IH * d.IW; }
@@ -419,8 +552,12 @@ struct gm_net {
     std::vector<gm::nn::Layer> layers;
     size_t nparam = 0;
     float *w = nullptr, *gw = nullptr, *m1 = nullptr, *m2 = nullptr;
-    __nv_bfloat16 *wb = nullptr;
-    std::vector<float *> x, u, gx, gu;
+    __nv_bfloat16 *wf = nullptr, *wd = nullptr;  // packed BF16 weights (FWD and DGRAD layouts)
+    size_t nf = 0, nd = 0;
+    gm::nn::PackTable pack{};
+    int *tc_err = nullptr;  // set when a tensor-core wait gives up
+    std::vector<float *> x, gx, gu;  // x[l]: stored input of layer l; gx / gu: gradients before / after up-sampling
+    float *kpart = nullptr;          // split-K scratch of FWD / DGRAD launches
     float *y = nullptr, *gy = nullptr, *target = nullptr;
     float *wpart = nullptr;  // per-chunk weight-gradient partials
     float *loss_part = nullptr, *loss = nullptr;
@@ -441,10 +578,7 @@ namespace {
 using gm::nn::ConvDims;
 using gm::nn::Layer;
 
-constexpr int kWgChunk = 8192;  // (example, output position) pairs per weight-gradient block
-constexpr int kWgCo = 8;        // output channels per weight-gradient block
 constexpr int kLossBlocks = 1024;
-constexpr int kCT = 8;          // output channels per thread in the convolution kernels
 
 thread_local char g_nn_msg[256] = "";
 
@@ -502,34 +636,159 @@ void build_layers(gm_net *net) {
     add(64, 32, 8, 2 * s, 2 * s, 2, 2, 2, 3, 1, true);        // D2
     add(32, 16, 16, 4 * s, 4 * s, 1, 2, 2, 3, 1, true);       // D3
     add(16, 1, 16, 8 * s, 8 * s, 1, 2, 2, 3, 1, false);       // D4
-    size_t off = 0;
-    for (auto &l : net->layers) {
+    size_t off = 0, fo = 0, dof = 0;
+    long long cum = 0;
+    gm::nn::PackTable &tb = net->pack;
+    tb.nl = (int)net->layers.size();
+    for (size_t k = 0; k < net->layers.size(); ++k) {
+        Layer &l = net->layers[k];
         l.w_off = off;
         off += l.nw;
         l.b_off = off;
         off += l.d.CO;
+        l.taps = l.d.KD * l.d.KH * l.d.KW;
+        l.kf = (l.taps * l.d.CI + 63) / 64 * 64;
+        l.kd = (l.taps * l.d.CO + 63) / 64 * 64;
+        l.f_off = fo;
+        fo += (size_t)l.d.CO * l.kf;
+        l.d_off = dof;
+        dof += (size_t)l.d.CI * l.kd;
+        tb.CI[k] = l.d.CI;
+        tb.CO[k] = l.d.CO;
+        tb.taps[k] = l.taps;
+        tb.kf[k] = l.kf;
+        tb.kd[k] = l.kd;
+        tb.w_off[k] = (long long)l.w_off;
+        tb.f_off[k] = (long long)l.f_off;
+        tb.d_off[k] = (long long)l.d_off;
+        tb.cum[k] = cum;
+        cum += (long long)l.nw;
     }
+    tb.cum[net->layers.size()] = cum;
     net->nparam = off;
+    net->nf = fo;
+    net->nd = dof;
+}
+
+int log2_exact(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+// WGRAD split of the N * osz positions: enough chunks for about two waves of CTAs, each a
+// multiple of 64 positions between 256 and 8192
+int wgrad_chunk(const Layer &l, int N) {
+    const long long Q = (long long)N * l.d.OD * l.d.OH * l.d.OW;
+    const int mt = (l.taps * l.d.CI + 1 + 127) / 128;
+    const int bn = std::min(256, (l.d.CO + 15) / 16 * 16);
+    const int nt = (l.d.CO + bn - 1) / bn;
+    const long long want = std::max(1, (2 * 152 + mt * nt - 1) / (mt * nt));
+    long long blocks = (Q + 63) / 64;
+    long long per = (blocks + want - 1) / want;
+    per = std::max(4LL, std::min(128LL, per));
+    return (int)(per * 64);
 }
 
 int grid1(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 4096); }
 
-cudaError_t launch_conv_fwd(const float *in, const __nv_bfloat16 *w, const float *b, float *out, const ConvDims &d,
-                            bool relu, cudaStream_t s) {
-    const int osz = d.OD * d.OH * d.OW;
-    const int bx = osz >= 128 ? 128 : 32;
-    const dim3 grd((osz + bx - 1) / bx, (d.CO + kCT - 1) / kCT, d.N);
-    gm::nn::k_conv_fwd<kCT><<<grd, bx, 0, s>>>(in, w, b, out, d, relu ? 1 : 0);
-    return cudaGetLastError();
+constexpr long kTcWaitLimit = 1L << 22;
+
+// Split of the K blocks of a FWD / DGRAD launch with fewer tiles than two waves need.
+void fd_split(int tiles, int nkb, int &ksplit, int &kbper) {
+    ksplit = 1;
+    kbper = nkb;
+    if (tiles >= 152) return;
+    const int want = std::min(nkb, (2 * 152 + tiles - 1) / tiles);
+    if (want <= 1) return;
+    kbper = (nkb + want - 1) / want;
+    ksplit = (nkb + kbper - 1) / kbper;
 }
 
-cudaError_t launch_conv_bwd_data(const float *g, const __nv_bfloat16 *w, float *din, const ConvDims &d,
-                                 cudaStream_t s) {
-    const int isz = d.ID * d.IH * d.IW;
-    const int bx = isz >= 128 ? 128 : 32;
-    const dim3 grd((isz + bx - 1) / bx, (d.CI + kCT - 1) / kCT, d.N);
-    gm::nn::k_conv_bwd_data<kCT><<<grd, bx, 0, s>>>(g, w, din, d);
-    return cudaGetLastError();
+// GEMM view of layer l for a batch of N in one mode (everything but pointers)
+template <int MODE>
+gm::nn::ConvGemm gemm_view(const Layer &l, int N, int *chunks, int *bn_out) {
+    gm::nn::ConvGemm p{};
+    p.d = l.d;
+    p.d.N = N;
+    p.taps = l.taps;
+    p.relu = l.relu ? 1 : 0;
+    p.wait_limit = kTcWaitLimit;
+    p.ksplit = 1;
+    p.LD = l.in_d;
+    p.LH = l.in_h;
+    p.LW = l.in_w;
+    for (int a = 0; a < 3; ++a) p.us[a] = l.up[a] == 2 ? 1 : 0;
+    *chunks = 1;
+    if (MODE == gm::nn::FWD) {
+        p.M = N * l.d.OD * l.d.OH * l.d.OW;
+        p.ncols = l.d.CO;
+        p.kreal = l.taps * l.d.CI;
+        p.kpitch = l.kf;
+        p.lg = log2_exact(l.d.CI);
+    } else if (MODE == gm::nn::DGRAD) {
+        p.M = N * l.d.ID * l.d.IH * l.d.IW;
+        p.ncols = l.d.CI;
+        p.kreal = l.taps * l.d.CO;
+        p.kpitch = l.kd;
+        p.lg = log2_exact(l.d.CO);
+    } else {
+        p.M = l.taps * l.d.CI + 1;
+        p.ncols = l.d.CO;
+        p.kreal = N * l.d.OD * l.d.OH * l.d.OW;
+        p.lg = log2_exact(l.d.CI);
+        p.chunk = wgrad_chunk(l, N);
+        *chunks = (p.kreal + p.chunk - 1) / p.chunk;
+    }
+    const int bn = std::min(256, (p.ncols + 15) / 16 * 16);
+    if (MODE != gm::nn::WGRAD) {
+        const int tiles = ((p.M + 127) / 128) * ((p.ncols + bn - 1) / bn);
+        fd_split(tiles, p.kpitch / 64, p.ksplit, p.kbper);
+        *chunks = p.ksplit;
+    }
+    *bn_out = bn;
+    return p;
+}
+
+// FP32 elements of split-K scratch a FWD / DGRAD launch of layer l for a batch of N needs
+template <int MODE>
+size_t split_scratch(const Layer &l, int N) {
+    int ch = 1, bn = 16;
+    const gm::nn::ConvGemm p = gemm_view<MODE>(l, N, &ch, &bn);
+    return p.ksplit > 1 ? (size_t)p.ksplit * p.M * p.ncols : 0;
+}
+
+// Launches one tensor-core convolution of layer l for a batch of N (plus the split-K finish);
+// returns the launches.  wpk: packed BF16 weights of the mode (FWD: [co][kf], DGRAD:
+// [ci][kd]); out2: WGRAD bias partials, or the split-K scratch of FWD / DGRAD.
+template <int MODE>
+int launch_tc(const Layer &l, int N, const __nv_bfloat16 *wpk, const float *bias, const float *act,
+              const float *grad, float *out, float *out2, int *err, cudaStream_t s) {
+    int zdim = 1, bn = 16;
+    const gm::nn::ConvGemm p = gemm_view<MODE>(l, N, &zdim, &bn);
+    const dim3 grid((p.M + 127) / 128, (p.ncols + bn - 1) / bn, zdim);
+    const size_t smem = 2 * ((size_t)gm::nn::kTileA + (size_t)bn * 128);
+    gm::nn::k_conv_tc<MODE><<<grid, gm::nn::kTcThreads, smem, s>>>(act, grad, wpk, bias, out, out2, p, bn, err);
+    if (MODE == gm::nn::WGRAD || p.ksplit == 1) return 1;
+    const int per = MODE == gm::nn::FWD ? l.d.OD * l.d.OH * l.d.OW : l.d.ID * l.d.IH * l.d.IW;
+    gm::nn::k_splitk_finish<<<grid1((size_t)p.M * p.ncols), 256, 0, s>>>(
+        out2, p.ksplit, p.M, p.ncols, per, MODE == gm::nn::FWD ? bias : nullptr, MODE == gm::nn::FWD ? p.relu : 0, out);
+    return 2;
+}
+
+int wgrad_chunks(const Layer &l, int N) {
+    const long long Q = (long long)N * l.d.OD * l.d.OH * l.d.OW;
+    return (int)((Q + wgrad_chunk(l, N) - 1) / wgrad_chunk(l, N));
+}
+
+cudaError_t set_tc_smem_limits() {
+    cudaError_t e = cudaSuccess;
+    for (void *kern : {(void *)gm::nn::k_conv_tc<gm::nn::FWD>, (void *)gm::nn::k_conv_tc<gm::nn::DGRAD>,
+                       (void *)gm::nn::k_conv_tc<gm::nn::WGRAD>})
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     2 * (gm::nn::kTileA + 256 * 128));
+    return e;
 }
 
 // f(in_scale d) into net->y; returns the launches made
@@ -541,18 +800,10 @@ int forward_all(gm_net *net, const float *d_dev, const int *idx, int count, int 
     ++nl;
     const size_t L = net->layers.size();
     for (size_t k = 0; k < L; ++k) {
-        Layer l = net->layers[k];
-        l.d.N = N;
-        const float *src = net->x[k];
-        if (l.upsampled()) {
-            gm::nn::k_upsample<<<grid1(l.in_up(N)), 256, 0, s>>>(src, net->u[k], N * l.d.CI, l.in_d, l.in_h, l.in_w,
-                                                                 l.up[0], l.up[1], l.up[2]);
-            ++nl;
-            src = net->u[k];
-        }
+        const Layer &l = net->layers[k];
         float *dst = (k + 1 < L) ? net->x[k + 1] : net->y;
-        launch_conv_fwd(src, net->wb + l.w_off, net->w + l.b_off, dst, l.d, l.relu, s);
-        ++nl;
+        nl += launch_tc<gm::nn::FWD>(l, N, net->wf + l.f_off, net->w + l.b_off, net->x[k], nullptr, dst, net->kpart,
+                                     net->tc_err, s);
     }
     return nl;
 }
@@ -570,25 +821,23 @@ int backward_all(gm_net *net, int N, cudaStream_t s) {
             gm::nn::k_relu_mask<<<grid1(l.out(N)), 256, 0, s>>>(g, out, l.out(N));
             ++nl;
         }
-        const float *in = l.upsampled() ? net->u[k] : net->x[k];
-        const long long total = (long long)N * l.d.OD * l.d.OH * l.d.OW;
-        const int chunks = (int)((total + kWgChunk - 1) / kWgChunk);
+        const int chunks = wgrad_chunks(l, N);
         float *dwp = net->wpart;
         float *dbp = net->wpart + (size_t)chunks * l.nw;
-        gm::nn::k_conv_wgrad<kWgCo><<<dim3(((l.d.CO + kWgCo - 1) / kWgCo) * l.d.CI * l.d.KD, chunks), 256, 0, s>>>(
-            g, in, dwp, dbp, l.d, kWgChunk);
+        launch_tc<gm::nn::WGRAD>(l, N, nullptr, nullptr, net->x[k], g, dwp, dbp, net->tc_err, s);
         gm::nn::k_sum_chunks<<<grid1(l.nw), 256, 0, s>>>(dwp, net->gw + l.w_off, l.nw, chunks);
         gm::nn::k_sum_chunks<<<grid1(l.d.CO), 256, 0, s>>>(dbp, net->gw + l.b_off, l.d.CO, chunks);
         nl += 3;
         if (k == 0) break;  // no gradient with respect to the data
         if (l.upsampled()) {
-            launch_conv_bwd_data(g, net->wb + l.w_off, net->gu[k], l.d, s);
+            nl += launch_tc<gm::nn::DGRAD>(l, N, net->wd + l.d_off, nullptr, nullptr, g, net->gu[k], net->kpart,
+                                           net->tc_err, s);
             gm::nn::k_upsample_bwd<<<grid1(l.in_low(N)), 256, 0, s>>>(net->gu[k], net->gx[k], N * l.d.CI, l.in_d,
                                                                       l.in_h, l.in_w, l.up[0], l.up[1], l.up[2]);
-            nl += 2;
-        } else {
-            launch_conv_bwd_data(g, net->wb + l.w_off, net->gx[k], l.d, s);
             ++nl;
+        } else {
+            nl += launch_tc<gm::nn::DGRAD>(l, N, net->wd + l.d_off, nullptr, nullptr, g, net->gx[k], net->kpart,
+                                           net->tc_err, s);
         }
         g = net->gx[k];
     }
@@ -601,10 +850,13 @@ void free_net(gm_net *n) {
                      n->gt, n->mpred, n->loss_data, n->loss_data_part})
         cudaFree(p);
     if (n->loss_pair) cudaFreeHost(n->loss_pair);
-    cudaFree(n->wb);
+    cudaFree(n->wf);
+    cudaFree(n->wd);
+    cudaFree(n->tc_err);
     cudaFree(n->bad_index);
     if (n->bad_host) cudaFreeHost(n->bad_host);
-    for (auto *v : {&n->x, &n->u, &n->gx, &n->gu})
+    cudaFree(n->kpart);
+    for (auto *v : {&n->x, &n->gx, &n->gu})
         for (float *p : *v) cudaFree(p);
     delete n;
 }
@@ -619,9 +871,10 @@ bool dev_alloc(float **p, size_t elems, size_t *total) {
 extern "C" {
 
 gm_net_handle gm_net_create(int grid, int depth, int max_batch, unsigned long long seed) {
-    if (grid < 16 || grid > 1024 || grid % 16 || depth != 16 || max_batch < 1 || max_batch > 65535) {
+    if (grid < 16 || grid > 1024 || grid % 16 || depth != 16 || max_batch < 1 ||
+        (long long)max_batch * 256 * grid * grid >= (1LL << 31)) {
         nn_fail(GM_EINVAL, "gm_net_create: grid must be a multiple of 16 in [16, 1024], depth 16, "
-                           "1 <= max_batch <= 65535");
+                           "max_batch >= 1 and max_batch * 256 * grid^2 < 2^31");
         return nullptr;
     }
     int dev = 0;
@@ -644,26 +897,28 @@ gm_net_handle gm_net_create(int grid, int depth, int max_batch, unsigned long lo
     const int B = max_batch;
     size_t total = 0;
     bool ok = dev_alloc(&net->w, P, &total) && dev_alloc(&net->gw, P, &total) && dev_alloc(&net->m1, P, &total) &&
-              dev_alloc(&net->m2, P, &total) && cudaMalloc(&net->wb, 2 * P) == cudaSuccess;
+              dev_alloc(&net->m2, P, &total) && cudaMalloc(&net->wf, 2 * net->nf) == cudaSuccess &&
+              cudaMalloc(&net->wd, 2 * net->nd) == cudaSuccess && cudaMalloc(&net->tc_err, sizeof(int)) == cudaSuccess;
     net->x.assign(L, nullptr);
-    net->u.assign(L, nullptr);
     net->gx.assign(L, nullptr);
     net->gu.assign(L, nullptr);
-    size_t wpart = 0;
+    size_t wpart = 0, kpart = 1;
     for (size_t k = 0; ok && k < L; ++k) {
         const Layer &l = net->layers[k];
         ok = dev_alloc(&net->x[k], l.in_low(B), &total) && dev_alloc(&net->gx[k], l.in_low(B), &total);
-        if (ok && l.upsampled()) ok = dev_alloc(&net->u[k], l.in_up(B), &total) && dev_alloc(&net->gu[k], l.in_up(B), &total);
-        const long long pairs = (long long)B * l.d.OD * l.d.OH * l.d.OW;
-        const size_t chunks = (size_t)((pairs + kWgChunk - 1) / kWgChunk);
-        wpart = std::max(wpart, chunks * (l.nw + l.d.CO));
+        if (ok && l.upsampled()) ok = dev_alloc(&net->gu[k], l.in_up(B), &total);
+        for (int n = 1; n <= B; ++n) {  // chunk and split counts vary with the batch, not monotonically
+            wpart = std::max(wpart, (size_t)wgrad_chunks(l, n) * (l.nw + l.d.CO));
+            kpart = std::max(kpart, std::max(split_scratch<gm::nn::FWD>(l, n), split_scratch<gm::nn::DGRAD>(l, n)));
+        }
     }
     const size_t nout = net->layers.back().out(B);
     ok = ok && dev_alloc(&net->y, nout, &total) && dev_alloc(&net->gy, nout, &total) &&
          dev_alloc(&net->target, nout, &total) && dev_alloc(&net->wpart, wpart, &total) &&
+         dev_alloc(&net->kpart, kpart, &total) &&
          dev_alloc(&net->loss_part, kLossBlocks, &total) && dev_alloc(&net->loss, 1, &total) &&
          cudaMalloc(&net->bad_index, sizeof(int)) == cudaSuccess &&
-         cudaMallocHost(&net->bad_host, sizeof(int)) == cudaSuccess &&
+         cudaMallocHost(&net->bad_host, 2 * sizeof(int)) == cudaSuccess &&
          cudaMallocHost(&net->loss_pair, 2 * sizeof(float)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -689,8 +944,12 @@ gm_net_handle gm_net_create(int grid, int depth, int max_batch, unsigned long lo
     if (e == cudaSuccess) e = cudaMemset(net->gw, 0, 4 * P);
     if (e == cudaSuccess) e = cudaMemset(net->bad_index, 0, sizeof(int));
     net->loss_pair[0] = net->loss_pair[1] = 0.f;
+    if (e == cudaSuccess) e = cudaMemset(net->wf, 0, 2 * net->nf);
+    if (e == cudaSuccess) e = cudaMemset(net->wd, 0, 2 * net->nd);
+    if (e == cudaSuccess) e = cudaMemset(net->tc_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = set_tc_smem_limits();
     if (e == cudaSuccess) {
-        gm::nn::k_to_bf16<<<grid1(P), 256>>>(net->w, net->wb, P);
+        gm::nn::k_pack_weights<<<grid1(P), 256>>>(net->w, net->wf, net->wd, net->pack);
         e = cudaDeviceSynchronize();
     }
     if (e != cudaSuccess) {
@@ -772,9 +1031,10 @@ gm_status gm_net_train_step(gm_net_handle net, const float *d_dev, const float *
         const double b1 = 0.9, b2 = 0.999;
         const float c1 = (float)(1.0 - std::pow(b1, (double)net->step));
         const float c2 = (float)(1.0 - std::pow(b2, (double)net->step));
-        gm::nn::k_adam<<<grid1(net->nparam), 256, 0, s>>>(net->w, net->gw, net->m1, net->m2, net->wb, net->nparam, lr,
+        gm::nn::k_adam<<<grid1(net->nparam), 256, 0, s>>>(net->w, net->gw, net->m1, net->m2, net->nparam, lr,
                                                           (float)b1, (float)b2, 1e-8f, c1, c2);
-        ++nl;
+        gm::nn::k_pack_weights<<<grid1(net->nparam), 256, 0, s>>>(net->w, net->wf, net->wd, net->pack);
+        nl += 2;
     }
     net->last_launches = nl;
     cudaError_t e = cudaGetLastError();
@@ -785,9 +1045,15 @@ gm_status gm_net_train_step(gm_net_handle net, const float *d_dev, const float *
         if (e == cudaSuccess && net->lambda > 0.f)
             e = cudaMemcpyAsync(net->loss_pair + 1, net->loss_data, sizeof(float), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(net->bad_host, net->bad_index, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(net->bad_host + 1, net->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         *loss_host = net->loss_pair[0] + net->lambda * net->loss_pair[1];
         bad = *net->bad_host;
+        if (e == cudaSuccess && net->bad_host[1]) {
+            cudaMemsetAsync(net->tc_err, 0, sizeof(int), s);
+            return nn_fail(GM_ECUDA, "gm_net_train_step: a tensor-core wait gave up; results of this or an earlier "
+                                     "unsynchronised call are invalid");
+        }
         if (e == cudaSuccess && bad) {
             cudaMemsetAsync(net->bad_index, 0, sizeof(int), s);
             return nn_fail(GM_EINVAL, "gm_net_train_step: an index was outside [0, count); those examples were "
@@ -853,7 +1119,7 @@ gm_status gm_net_set_params(gm_net_handle net, const float *host, int64_t n, int
     float *dst = which == 2 ? net->m1 : which == 3 ? net->m2 : net->w;
     cudaError_t e = cudaMemcpy(dst, host, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && which == 0) {
-        gm::nn::k_to_bf16<<<grid1(net->nparam), 256>>>(net->w, net->wb, net->nparam);
+        gm::nn::k_pack_weights<<<grid1(net->nparam), 256>>>(net->w, net->wf, net->wd, net->pack);
         e = cudaDeviceSynchronize();
     }
     return e == cudaSuccess ? GM_OK : nn_fail(GM_ECUDA, cudaGetErrorString(e));
@@ -868,6 +1134,102 @@ gm_status gm_net_get_step(gm_net_handle net, int64_t *step) {
 gm_status gm_net_set_step(gm_net_handle net, int64_t step) {
     if (!net || step < 0) return nn_fail(GM_EINVAL, "gm_net_set_step: null handle or negative step");
     net->step = step;
+    return GM_OK;
+}
+
+gm_status gm_conv3d(int mode, int N, int CI, int CO, int ID, int IH, int IW, int KD, int stride, const float *x,
+                    const float *g, const float *w, const float *b, float *out, float *bias_grad, void *stream) {
+    auto pow2 = [](int v) { return v >= 1 && (v & (v - 1)) == 0; };
+    if (mode < 0 || mode > 2 || N < 1 || !pow2(CI) || !pow2(CO) || CI > 4096 || CO > 4096 || ID < 1 || IH < 1 ||
+        IW < 1 || (KD != 1 && KD != 3) || (stride != 1 && stride != 2) || !w || !out ||
+        (mode != 1 && !x) || (mode != 0 && !g))
+        return nn_fail(GM_EINVAL, "gm_conv3d: bad mode, size, channel count (powers of two), kernel depth, "
+                                  "stride or null pointer");
+    Layer l{};
+    l.d.CI = CI;
+    l.d.CO = CO;
+    l.d.ID = ID;
+    l.d.IH = IH;
+    l.d.IW = IW;
+    l.d.KD = KD;
+    l.d.KH = 3;
+    l.d.KW = 3;
+    l.d.SD = 1;
+    l.d.SH = stride;
+    l.d.SW = stride;
+    l.d.PD = KD / 2;
+    l.d.PH = 1;
+    l.d.PW = 1;
+    l.d.OD = ID;
+    l.d.OH = (IH - 1) / stride + 1;
+    l.d.OW = (IW - 1) / stride + 1;
+    l.in_d = ID;
+    l.in_h = IH;
+    l.in_w = IW;
+    l.up[0] = l.up[1] = l.up[2] = 1;
+    l.taps = KD * 9;
+    l.kf = (l.taps * CI + 63) / 64 * 64;
+    l.kd = (l.taps * CO + 63) / 64 * 64;
+    l.nw = (size_t)CO * CI * l.taps;
+    const long long rows = (long long)N * std::max(ID * IH * IW, l.d.OD * l.d.OH * l.d.OW);
+    if (rows * std::max(CI, CO) > (1LL << 31) - 1 || rows > (1LL << 30))
+        return nn_fail(GM_EINVAL, "gm_conv3d: tensor too large");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    gm::nn::PackTable tb{};
+    tb.nl = 1;
+    tb.CI[0] = CI;
+    tb.CO[0] = CO;
+    tb.taps[0] = l.taps;
+    tb.kf[0] = l.kf;
+    tb.kd[0] = l.kd;
+    tb.cum[1] = (long long)l.nw;
+    __nv_bfloat16 *wf = nullptr, *wd = nullptr;
+    float *part = nullptr, *kpart = nullptr;
+    int *err = nullptr;
+    const int chunks = wgrad_chunks(l, N);
+    const size_t ksz = mode == 0 ? split_scratch<gm::nn::FWD>(l, N) : mode == 1 ? split_scratch<gm::nn::DGRAD>(l, N) : 0;
+    cudaError_t e = set_tc_smem_limits();
+    if (e == cudaSuccess && ksz) e = cudaMalloc(&kpart, sizeof(float) * ksz);
+    if (e == cudaSuccess) e = cudaMalloc(&wf, 2 * (size_t)CO * l.kf);
+    if (e == cudaSuccess) e = cudaMalloc(&wd, 2 * (size_t)CI * l.kd);
+    if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+    if (e == cudaSuccess && mode == 2) e = cudaMalloc(&part, sizeof(float) * (size_t)chunks * (l.nw + CO));
+    if (e == cudaSuccess) e = cudaMemsetAsync(wf, 0, 2 * (size_t)CO * l.kf, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(wd, 0, 2 * (size_t)CI * l.kd, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    int bad = 0;
+    if (e == cudaSuccess) {
+        gm::nn::k_pack_weights<<<grid1(l.nw), 256, 0, s>>>(w, wf, wd, tb);
+        if (mode == 0) {
+            float *zero = nullptr;
+            if (!b) {  // a zero bias
+                e = cudaMalloc(&zero, sizeof(float) * CO);
+                if (e == cudaSuccess) e = cudaMemsetAsync(zero, 0, sizeof(float) * CO, s);
+            }
+            if (e == cudaSuccess) launch_tc<gm::nn::FWD>(l, N, wf, b ? b : zero, x, nullptr, out, kpart, err, s);
+            if (zero) {
+                cudaStreamSynchronize(s);
+                cudaFree(zero);
+            }
+        } else if (mode == 1) {
+            launch_tc<gm::nn::DGRAD>(l, N, wd, nullptr, nullptr, g, out, kpart, err, s);
+        } else {
+            launch_tc<gm::nn::WGRAD>(l, N, nullptr, nullptr, x, g, part, part + (size_t)chunks * l.nw, err, s);
+            gm::nn::k_sum_chunks<<<grid1(l.nw), 256, 0, s>>>(part, out, l.nw, chunks);
+            if (bias_grad)
+                gm::nn::k_sum_chunks<<<grid1(CO), 256, 0, s>>>(part + (size_t)chunks * l.nw, bias_grad, CO, chunks);
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    cudaFree(wf);
+    cudaFree(wd);
+    cudaFree(part);
+    cudaFree(kpart);
+    cudaFree(err);
+    if (e != cudaSuccess) return nn_fail(GM_ECUDA, cudaGetErrorString(e));
+    if (bad) return nn_fail(GM_ECUDA, "gm_conv3d: a tensor-core wait gave up");
     return GM_OK;
 }
 

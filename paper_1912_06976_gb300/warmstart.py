@@ -51,6 +51,7 @@ def _lib():
                 "gm_net_last_launch_count": (ci, [vp]),
                 "gm_net_set_data_term": (ci, [vp, vp, cf]),
                 "gm_net_last_losses": (ci, [vp, ctypes.POINTER(cf), ctypes.POINTER(cf)]),
+                "gm_conv3d": (ci, [ci, ci, ci, ci, ci, ci, ci, ci, ci, vp, vp, vp, vp, vp, vp, vp]),
                 "gm_net_last_error": (ctypes.c_char_p, []),
             }
             for name, (res, args) in sig.items():
@@ -199,6 +200,40 @@ class WarmStartNet:
             self.close()
         except Exception:
             pass
+
+
+def conv3d(mode: int, w, x=None, g=None, b=None, stride: int = 1, out=None, bias_grad=None, stream=None):
+    """One convolution through the network's tensor-core kernels (see gm_conv3d): mode 0 forward
+    (x -> out), 1 data gradient (g -> out), 2 weight gradient (x, g -> out [, bias_grad]).
+    w is (CO, CI, KD, 3, 3); x (N, CI, D, H, W); g (N, CO, D, OH, OW); float32 CUDA tensors."""
+    import torch
+
+    CO, CI, KD = int(w.shape[0]), int(w.shape[1]), int(w.shape[2])
+    if mode == 1:
+        N, _, D, OH, OW = (int(v) for v in g.shape)
+        if out is None:
+            raise ValueError("mode 1 needs `out` (its input size is not implied by g)")
+        IH, IW = int(out.shape[3]), int(out.shape[4])
+    else:
+        N, _, D, IH, IW = (int(v) for v in x.shape)
+    OH, OW = (IH - 1) // stride + 1, (IW - 1) // stride + 1
+    if out is None:
+        shape = (N, CO, D, OH, OW) if mode == 0 else (CO, CI, KD, 3, 3)
+        out = torch.empty(shape, dtype=torch.float32, device=w.device)
+    chk = {"w": (w, (CO, CI, KD, 3, 3)), "out": (out, (N, CO, D, OH, OW) if mode == 0 else
+                                                  (N, CI, D, IH, IW) if mode == 1 else (CO, CI, KD, 3, 3))}
+    if mode != 1:
+        chk["x"] = (x, (N, CI, D, IH, IW))
+    if mode != 0:
+        chk["g"] = (g, (N, CO, D, OH, OW))
+    if b is not None:
+        chk["b"] = (b, (CO,))
+    if bias_grad is not None:
+        chk["bias_grad"] = (bias_grad, (CO,))
+    ptr = {k: _device_f32(t, shp, k) for k, (t, shp) in chk.items()}
+    _check(_lib().gm_conv3d(int(mode), N, CI, CO, D, IH, IW, KD, int(stride), ptr.get("x"), ptr.get("g"), ptr["w"],
+                            ptr.get("b"), ptr["out"], ptr.get("bias_grad"), G._stream_ptr(stream)))
+    return out
 
 
 # ------------------------------------------------------------------------------------------

@@ -1,10 +1,15 @@
-"""The warm-start network's CUDA kernels against the float64 CPU oracle of the same network.
+"""The warm-start network's tensor-core kernels against the float64 CPU oracle of the network.
 
-The library convolves with BF16 copies of its FP32 weights and accumulates in FP32; the oracle
-is handed the same BF16-rounded weights, so what remains is FP32 rounding in sums of up to
-27 * 128 products: outputs and gradients agree to a relative 2-norm error of 1e-4 (ReLU
-decisions near zero may flip between the two precisions; each flip moves the result by a
-value of the size of that rounding).
+Every convolution is a tcgen05 GEMM of BF16 operands (the BF16 weights, and the FP32
+activations and gradients rounded to BF16 as they are gathered) with FP32 accumulation; one
+convolution at a time agrees with the oracle to 1e-6 (tests/test_conv3d_tc_gpu.py).  Through
+the whole network the comparison is bounded by the BF16 rounding itself: the oracle rounds the
+same operands (``bf16_operands=True``), but an FP32-vs-float64 difference of 1e-7 in any sum
+moves some operand across a BF16 rounding boundary, and the 18 products of a step spread that
+to every output.  Perturbing the oracle's own sums by a relative 1e-7 moves its output by about
+4e-3 and its gradient by a few 1e-2 (on the networks tested here), the same size as the
+difference between BF16 and exact operands (5e-3 and 3e-2).  The bounds are TOL_FWD = 2e-2 on
+outputs and TOL_GRAD = 1e-1 on gradients (0.2 per layer); an indexing error gives O(1).
 """
 import numpy as np
 import pytest
@@ -13,7 +18,9 @@ from oracle import warmstart_net as N
 from tests.conftest import rel_err
 
 pytestmark = pytest.mark.gpu
-TOL = 1e-4
+TOL_FWD = 2e-2
+TOL_GRAD = 1e-1
+TOL_LOSS = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -49,10 +56,12 @@ def test_forward_matches_oracle(ws, S, batch):
     d, _ = _inputs(S, batch, 1)
     got = net.forward(_cuda(d)).cpu().numpy()
     p = N.conv_weights_bf16(net.get_params())
-    ref = N.forward(p, d.astype(np.float64), 0.8, 1.7)
+    ref = N.forward(p, d.astype(np.float64), 0.8, 1.7, bf16_operands=True)
     assert got.shape == (batch, 16, S, S)
-    assert rel_err(got, ref) < TOL
-    assert net.last_launch_count() == 1 + 9 + 4 + 1  # gather+scale, 9 convs, 4 up-samplings, output scale
+    err = rel_err(got, ref)
+    assert err < TOL_FWD, err
+    # gather + scale, 9 convolutions (up-sampling folded in), their split-K finishes, output scale
+    assert 11 <= net.last_launch_count() <= 20
     net.close()
 
 
@@ -73,11 +82,11 @@ def test_loss_and_gradient_match_oracle(ws, S):
     loss = net.train_step(_cuda(d), _cuda(m), 0.0)
     g = net.get_params("grad").astype(np.float64)
     p = N.conv_weights_bf16(net.get_params())
-    ref_loss, ref_g = N.loss_and_grad(p, d.astype(np.float64), m.astype(np.float64), 1.1, 0.6)
-    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    ref_loss, ref_g = N.loss_and_grad(p, d.astype(np.float64), m.astype(np.float64), 1.1, 0.6, bf16_operands=True)
+    assert abs(loss - ref_loss) <= TOL_LOSS * ref_loss
     per_layer = [(rel_err(g[ws_], ref_g[ws_]), rel_err(g[bs], ref_g[bs])) for ws_, bs in _layer_slices()]
-    assert rel_err(g, ref_g) < TOL, per_layer
-    assert max(max(e) for e in per_layer) < 10 * TOL, per_layer  # every layer's weights and biases
+    assert rel_err(g, ref_g) < TOL_GRAD, per_layer
+    assert max(max(e) for e in per_layer) < 2 * TOL_GRAD, per_layer  # every layer's weights and biases
     assert net.step == 0  # lr = 0: no Adam step
     net.close()
 
@@ -183,12 +192,13 @@ def test_data_term_loss_and_gradient_match_oracle(ws, gm):
     model_term, data_term = net.last_losses()
     g = net.get_params("grad").astype(np.float64)
     p = N.conv_weights_bf16(net.get_params())
-    ref_loss, ref_g = N.loss_and_grad(p, d.astype(np.float64), m.astype(np.float64), 0.3, 0.8, Gd, 0.5)
-    ref_model = N.loss(p, d.astype(np.float64), m.astype(np.float64), 0.3, 0.8)
-    assert abs(model_term - ref_model) <= 1e-5 * ref_model
-    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    ref_loss, ref_g = N.loss_and_grad(p, d.astype(np.float64), m.astype(np.float64), 0.3, 0.8, Gd, 0.5,
+                                      bf16_operands=True)
+    ref_model = N.loss(p, d.astype(np.float64), m.astype(np.float64), 0.3, 0.8, bf16_operands=True)
+    assert abs(model_term - ref_model) <= TOL_LOSS * ref_model
+    assert abs(loss - ref_loss) <= TOL_LOSS * ref_loss
     assert abs(loss - (model_term + 0.5 * data_term)) <= 1e-6 * loss
-    assert rel_err(g, ref_g) < TOL
+    assert rel_err(g, ref_g) < TOL_GRAD, rel_err(g, ref_g)
     # lambda = 0 removes the term again
     net.set_data_term(None, 0.0)
     net.train_step(_cuda(d), _cuda(m), 0.0)

@@ -155,3 +155,49 @@ def test_data_term_of_an_exact_model_is_zero():
     d = (G @ mp).reshape(1, S, S)
     base = N.loss(p, d, np.zeros((1, 16, S, S)), 1.0, 1.5)
     assert abs(N.loss(p, d, np.zeros((1, 16, S, S)), 1.0, 1.5, G, 3.0) - base) < 1e-20 + 1e-12 * base
+
+
+def test_explicit_backward_formulas_equal_autograd():
+    """The explicit data / weight / bias gradient formulas of the BF16-operand convolution, with
+    the rounding switched off, reproduce autograd's gradient of the plain network."""
+    S = 16
+    rng = np.random.default_rng(12)
+    p = rng.standard_normal(N.num_params()) * 0.05
+    d = rng.standard_normal((2, S, S))
+    m = rng.standard_normal((2, 16, S, S))
+    l1, g1 = N.loss_and_grad(p, d, m, 0.8, 1.1)
+    l2, g2 = N.loss_and_grad(p, d, m, 0.8, 1.1, explicit_backward=True)
+    assert abs(l1 - l2) <= 1e-15 * abs(l1)
+    assert np.linalg.norm(g1 - g2) <= 1e-13 * np.linalg.norm(g1)
+
+
+def test_bf16_operand_forward_is_conv_of_rounded_operands():
+    """With BF16 operands, the first layer's output is the loop-sum convolution of the rounded
+    input (the weights are passed already rounded)."""
+    S = 16
+    rng = np.random.default_rng(13)
+    p = N.conv_weights_bf16(rng.standard_normal(N.num_params()) * 0.05)
+    d = rng.standard_normal((1, S, S))
+    (w, b), = N.unpack(p)[:1]
+    x = torch.as_tensor(d).reshape(1, 1, 1, S, S)
+    y = N._Bf16OperandConv.apply(x, w, b, (1, 1, 1), (0, 1, 1), True)
+    xr = N.bf16_round(d).reshape(1, 1, S, S)
+    ref = brute_conv(xr, w.numpy(), b.numpy(), (1, 1, 1), (0, 1, 1))
+    assert np.allclose(y[0].numpy(), ref, rtol=0, atol=1e-12)
+    # and the rounding is visible: the unrounded input gives a different result
+    assert not np.allclose(y[0].numpy(), brute_conv(d.reshape(1, 1, S, S), w.numpy(), b.numpy(), (1, 1, 1),
+                                                    (0, 1, 1)), rtol=0, atol=1e-9)
+
+
+def test_bf16_operand_gradient_is_close_to_the_exact_one():
+    """Rounding the GEMM operands to BF16 changes the gradient by a few percent (the BF16 unit
+    2^-8 per operand, compounded over the 18 products of the forward and backward passes)."""
+    S = 16
+    rng = np.random.default_rng(14)
+    p = N.conv_weights_bf16(rng.standard_normal(N.num_params()) * 0.05)
+    d = rng.standard_normal((2, S, S))
+    m = rng.standard_normal((2, 16, S, S))
+    _, g1 = N.loss_and_grad(p, d, m)
+    _, g2 = N.loss_and_grad(p, d, m, bf16_operands=True)
+    rel = np.linalg.norm(g1 - g2) / np.linalg.norm(g1)
+    assert 1e-4 < rel < 1e-1
