@@ -5,6 +5,7 @@
 //                     -> sum of groups + inverse column FFT (K5b) -> rows c2r + window (K6)
 // transpose m' = G^T d: rows r2c of d (K7) -> column FFT of d, then per layer conj(S) x and
 //                     inverse column FFT (K8) -> rows c2r + window (K9)
+#include <cstdint>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,9 +51,16 @@ cudaError_t rows_r2c(const R *in, int rows, int row_len, int nlayers, cpx_t<R> *
 
 template <typename R, int X1, int X2, int PAIRS, int THREADS>
 cudaError_t rows_c2r_p(const cpx_t<R> *in, long long ld_k, long long ld_layer, long long ld_row, int rows,
-                       int nlayers, R *out, int row_len_out, double scale, const void *tw, cudaStream_t s) {
+                       int nlayers, R *out, int row_len_out, double scale, const void *tw, bool discard,
+                       cudaStream_t s) {
     using C = cpx_t<R>;
     constexpr int N = X1 * X2, Kx = N / 2 + 1;
+    // the block's run of 2*PAIRS rows per (k, layer) must be whole, aligned 128-byte lines
+    constexpr long long LINE = 128 / (long long)sizeof(C);
+    const int disc = (discard && ld_row == 1 && (2 * PAIRS) % LINE == 0 && ld_k % LINE == 0 &&
+                      ld_layer % LINE == 0 && reinterpret_cast<uintptr_t>(in) % 128 == 0)
+                         ? 1
+                         : 0;
     // inverse radices (X2, X1): pass-2 items j < X2 write X2-wide coalesced rows
     const size_t sm = sizeof(C) * (2 * PAIRS * Kx + PAIRS * fast::Ex<X2, X1>::value);
     auto k = fast::k_rows_c2r<C, R, X2, X1, PAIRS, THREADS>;
@@ -60,18 +68,19 @@ cudaError_t rows_c2r_p(const cpx_t<R> *in, long long ld_k, long long ld_layer, l
     if (e != cudaSuccess) return e;
     dim3 grd((rows + 2 * PAIRS - 1) / (2 * PAIRS), nlayers);
     k<<<grd, THREADS, sm, s>>>(in, ld_k, ld_layer, ld_row, rows, out, row_len_out, scale,
-                               static_cast<const C *>(tw));
+                               static_cast<const C *>(tw), disc);
     return cudaGetLastError();
 }
 
 template <typename R, int X1, int X2>
 cudaError_t rows_c2r(const cpx_t<R> *in, long long ld_k, long long ld_layer, long long ld_row, int rows,
-                     int nlayers, R *out, int row_len_out, double scale, const void *tw, cudaStream_t s) {
+                     int nlayers, R *out, int row_len_out, double scale, const void *tw, bool discard,
+                     cudaStream_t s) {
     if (few_rows(rows, nlayers))
         return rows_c2r_p<R, X1, X2, 1, 32>(in, ld_k, ld_layer, ld_row, rows, nlayers, out, row_len_out, scale, tw,
-                                            s);
+                                            discard, s);
     return rows_c2r_p<R, X1, X2, kPairs, 256>(in, ld_k, ld_layer, ld_row, rows, nlayers, out, row_len_out, scale,
-                                              tw, s);
+                                              tw, discard, s);
 }
 
 // ---- y-direction (columns): forward radices (Y1, Y2)
@@ -167,9 +176,9 @@ cudaError_t x_r2c(int N, const R *in, int rows, int row_len, int nlayers, cpx_t<
 
 template <typename R>
 cudaError_t x_c2r(int N, const cpx_t<R> *in, long long ldk, long long ldl, long long ldr, int rows, int nlayers,
-                  R *out, int row_len_out, double scale, const void *tw, cudaStream_t s) {
+                  R *out, int row_len_out, double scale, const void *tw, bool discard, cudaStream_t s) {
 #define F(n, a, b) \
-    if (N == n) return rows_c2r<R, a, b>(in, ldk, ldl, ldr, rows, nlayers, out, row_len_out, scale, tw, s);
+    if (N == n) return rows_c2r<R, a, b>(in, ldk, ldl, ldr, rows, nlayers, out, row_len_out, scale, tw, discard, s);
     GM_X_SIZES(F)
 #undef F
     return cudaErrorNotSupported;
@@ -248,7 +257,7 @@ cudaError_t forward_fast_t(gm_plan *p, const R *m, R *d, cudaStream_t s, int *nl
     timing_end(p, s, t);
     t = timing_begin(p, s, K_FWD_C2R);
     // B is [kx][j]: element (k, row j) at k*sy + j
-    CK(x_c2r<R>(g.NPx, B, g.sy, 0, 1, g.sy, 1, d, g.sx, 1.0 / ((double)g.NPx * g.NPy), p->tw_x, s));
+    CK(x_c2r<R>(g.NPx, B, g.sy, 0, 1, g.sy, 1, d, g.sx, 1.0 / ((double)g.NPx * g.NPy), p->tw_x, false, s));
     timing_end(p, s, t);
     *nl = 3;
     return cudaSuccess;
@@ -269,8 +278,9 @@ cudaError_t transpose_fast_t(gm_plan *p, const R *d, R *m, cudaStream_t s, int *
     timing_end(p, s, t);
     t = timing_begin(p, s, K_TR_C2R);
     // A2 is [kx][r][q] with column pitch nyp: element (k, layer r, row q) at (k*nz + r)*nyp + q
+    // A2 is dead once read: its lines are dropped from L2 instead of being written back
     CK(x_c2r<R>(g.NPx, A2, (long long)g.nz * g.nyp, g.nyp, 1, g.ny, g.nz, m, g.nx, 1.0 / ((double)g.NPx * g.NPy),
-                p->tw_x, s));
+                p->tw_x, true, s));
     timing_end(p, s, t);
     *nl = 3;
     return cudaSuccess;

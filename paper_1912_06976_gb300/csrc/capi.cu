@@ -201,7 +201,7 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
     p->pxr = prm->pxr; p->pyr = prm->pyr;
     g.nx = prm->sx + prm->pxl + prm->pxr;
     g.ny = prm->sy + prm->pyl + prm->pyr;
-    g.nyp = g.ny + (g.ny & 1);
+    g.nyp = (g.ny + 15) / 16 * 16;  // intermediate column pitch: whole 128-byte lines per column
     p->Nx = g.sx + g.nx - 1;
     p->Ny = g.sy + g.ny - 1;
     g.NPx = gm_fft_length(p->Nx);

@@ -36,6 +36,55 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned int bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// L2 residency of the apply pipeline.  The spectrum and the input vector are each read once per
+// product: they are loaded with an evict-first policy so that they do not push the row-FFT
+// intermediates (written with evict-last) out of L2 between the kernel that writes them and the
+// kernel that reads them; the reader then discards the 128-byte lines it alone owns, so dead
+// intermediates are never written back to DRAM.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ float ld_hint(const float *p, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_hint(const double *p, uint64_t pol) {
+    double v;
+    asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float2 ld_hint(const float2 *p, uint64_t pol) {
+    float2 v;
+    asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double2 ld_hint(const double2 *p, uint64_t pol) {
+    double2 v;
+    asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_hint(float2 *p, float2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_hint(double2 *p, double2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol)
+                 : "memory");
+}
+// Drop the 128-byte L2 line at p (128-byte aligned) without writing it back; its contents
+// become undefined.  Only for lines that no thread reads again before they are rewritten.
+__device__ __forceinline__ void discard_line(const void *p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 template <int R1, bool INV, typename C>
 __device__ __forceinline__ void pass1_store(C (&v)[R1], C *ex, int j) {
     cl::Dft<R1, INV>::run(v);
@@ -88,13 +137,16 @@ template <typename C, typename Rin, int R1, int R2, int PAIRS, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_rows_r2c(const Rin *__restrict__ in, int rows, int row_len, int nlayers,
                                                       C *__restrict__ out, int out_rows, const C *__restrict__ tw) {
     constexpr int N = R1 * R2, EX = Ex<R1, R2>::value, Kx = N / 2 + 1;
-    static_assert(PAIRS * R2 <= THREADS && PAIRS * R1 <= THREADS, "one item of each pass per thread");
+    static_assert(THREADS == 32 * PAIRS && R1 <= 32 && R2 <= 32, "one warp per row pair, one item per lane");
     extern __shared__ unsigned char smem_raw[];
     C *ex = reinterpret_cast<C *>(smem_raw);
     const int q0 = blockIdx.x * 2 * PAIRS;
     const int layer = blockIdx.y;
-    for (int it = threadIdx.x; it < PAIRS * R2; it += THREADS) {
-        const int p = it / R2, j = it - p * R2;
+    const uint64_t pol_in = policy_evict_first(), pol_out = policy_evict_last();
+    // warp p transforms pair p on its own: both passes and the exchange stay inside the warp
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane < R2) {
+        const int p = wp, j = lane;
         const int qa = q0 + 2 * p;
         const bool va = qa < rows, vb = qa + 1 < rows;
         const Rin *ra = in + ((size_t)layer * rows + qa) * row_len;
@@ -103,28 +155,27 @@ __global__ void __launch_bounds__(THREADS) k_rows_r2c(const Rin *__restrict__ in
         for (int rr = 0; rr < R1; ++rr) {
             const int n = j + R2 * rr;
             const bool ok = n < row_len;
-            v[rr].x = (ok && va) ? (decltype(v[0].x))ra[n] : 0;
-            v[rr].y = (ok && vb) ? (decltype(v[0].x))ra[row_len + n] : 0;
+            v[rr].x = (ok && va) ? (decltype(v[0].x))ld_hint(ra + n, pol_in) : 0;
+            v[rr].y = (ok && vb) ? (decltype(v[0].x))ld_hint(ra + row_len + n, pol_in) : 0;
         }
         pass1_store<R1, false>(v, ex + p * EX, j);
     }
-    __syncthreads();
-    // pass 2 keeps its outputs in registers until every thread has read the exchange
+    __syncwarp();
+    // pass 2 keeps its outputs in registers until every lane has read the exchange
     C v[R2];
-    const int it2 = threadIdx.x;
-    const bool act = it2 < PAIRS * R1;
-    const int p2 = act ? it2 / R1 : 0, j2 = act ? it2 - p2 * R1 : 0;
+    const bool act = lane < R1;
+    const int p2 = wp, j2 = lane;
     if (act) {
         pass2_gather<R1, R2>(v, ex + p2 * EX, j2);
         pass2_twiddle_table<R1, R2, false>(v, tw, j2);
         cl::Dft<R2, false>::run(v);
     }
-    __syncthreads();
+    __syncwarp();
     if (act) {
 #pragma unroll
         for (int s = 0; s < R2; ++s) ex[p2 * EX + j2 + R1 * s] = v[s];  // natural order Z[k]
     }
-    __syncthreads();
+    __syncthreads();  // the separation below reads every pair (coalesced stores across pairs)
     // separate the two real rows: FFT(a)[k] = (Z[k] + conj Z[-k]) / 2, FFT(b)[k] = (Z[k] - conj Z[-k]) / 2i
 #pragma unroll 4
     for (int it = threadIdx.x; it < PAIRS * Kx; it += THREADS) {
@@ -139,8 +190,8 @@ __global__ void __launch_bounds__(THREADS) k_rows_r2c(const Rin *__restrict__ in
         x2.x = (a.y - b.y) * 0.5f;
         x2.y = (b.x - a.x) * 0.5f;
         C *o = out + ((size_t)k * nlayers + layer) * out_rows + qa;
-        o[0] = x1;
-        if (qa + 1 < rows) o[1] = x2;
+        st_hint(o, x1, pol_out);
+        if (qa + 1 < rows) st_hint(o + 1, x2, pol_out);
     }
 }
 
@@ -149,9 +200,13 @@ __global__ void __launch_bounds__(THREADS) k_rows_r2c(const Rin *__restrict__ in
 // X(k, layer, row) = in[k*ld_k + layer*ld_layer + row*ld_row], k < N/2+1; writes
 // out[layer][row][0:row_len_out] = scale * (inverse transform)[0:row_len_out].
 template <typename C, typename Rout, int R1, int R2, int PAIRS, int THREADS>
+// With discard_in, every (k, layer) run of the block's 2*PAIRS rows is whole 128-byte lines
+// (ld_row = 1, 128-byte aligned runs) that no other block reads: they are dropped from L2 once
+// read.
 __global__ void __launch_bounds__(THREADS) k_rows_c2r(const C *__restrict__ in, long long ld_k, long long ld_layer,
                                                       long long ld_row, int rows, Rout *__restrict__ out,
-                                                      int row_len_out, double scale, const C *__restrict__ tw) {
+                                                      int row_len_out, double scale, const C *__restrict__ tw,
+                                                      int discard_in) {
     constexpr int N = R1 * R2, EX = Ex<R1, R2>::value, Kx = N / 2 + 1, H = N / 2;
     extern __shared__ unsigned char smem_raw[];
     C *xs = reinterpret_cast<C *>(smem_raw);  // [2*PAIRS][Kx]
@@ -179,8 +234,19 @@ __global__ void __launch_bounds__(THREADS) k_rows_c2r(const C *__restrict__ in, 
         }
     }
     __syncthreads();
-    for (int it = threadIdx.x; it < PAIRS * R2; it += THREADS) {
-        const int p = it / R2, j = it - p * R2;
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    static_assert(THREADS == 32 * PAIRS && R1 <= 32 && R2 <= 32, "one warp per row pair, one item per lane");
+    constexpr int LINES = 2 * PAIRS * (int)sizeof(C) / 128;  // lines of one (k, layer) run
+    if constexpr (LINES > 0) {
+        if (discard_in) {
+            for (int it = threadIdx.x; it < Kx * LINES; it += THREADS) {
+                const int k = it / LINES, ln = it - k * LINES;
+                discard_line(in + k * ld_k + layer * ld_layer + q0 + ln * (128 / (int)sizeof(C)));
+            }
+        }
+    }
+    if (lane < R2) {  // warp p runs both passes of pair p
+        const int p = wp, j = lane;
         const C *x1r = xs + (2 * p) * Kx, *x2r = x1r + Kx;
         C v[R1];
 #pragma unroll
@@ -193,10 +259,10 @@ __global__ void __launch_bounds__(THREADS) k_rows_c2r(const C *__restrict__ in, 
         }
         pass1_store<R1, true>(v, ex + p * EX, j);
     }
-    __syncthreads();
+    __syncwarp();
     const auto sc = (decltype(ex[0].x))scale;
-    for (int it = threadIdx.x; it < PAIRS * R1; it += THREADS) {
-        const int p = it / R1, j = it - p * R1;
+    if (lane < R1) {
+        const int p = wp, j = lane;
         C v[R2];
         pass2_gather<R1, R2>(v, ex + p * EX, j);
         pass2_twiddle_table<R1, R2, true>(v, tw, j);
@@ -288,7 +354,9 @@ __global__ void __launch_bounds__(THREADS)
     C acc[R2];
 #pragma unroll
     for (int s = 0; s < R2; ++s) acc[s] = c_make<C>(0, 0);
+    const uint64_t pol_s = policy_evict_first();
     load_table<N, THREADS>(tw, twg);
+    const int row_lines = (ny * (int)sizeof(C) + 127) / 128;  // lines of one A column (pitch nyp: whole lines)
     for (int r = r_begin; r < r_end; r += LSTEP) {
         for (int it = t; it < COLS * LSTEP * R2; it += THREADS) {
             const int c = it / (LSTEP * R2);
@@ -306,6 +374,13 @@ __global__ void __launch_bounds__(THREADS)
             pass1_store<R1, false>(v, ex + (c * LSTEP + l) * EX, j);
         }
         __syncthreads();
+        // every A column of this step has been read by the whole block: drop its lines
+        for (int it = t; it < COLS * LSTEP * row_lines; it += THREADS) {
+            const int cl_ = it / row_lines, ln = it - cl_ * row_lines;
+            const int c = cl_ / LSTEP, l = cl_ - c * LSTEP;
+            const int kx = kx0 + c, rl = r + l;
+            if (kx < Kx && rl < r_end) discard_line(A + ((size_t)kx * nz + rl) * nyp + ln * (128 / (int)sizeof(C)));
+        }
         if (owner && okx < Kx) {
 #pragma unroll
             for (int l = 0; l < LSTEP; ++l) {
@@ -317,7 +392,7 @@ __global__ void __launch_bounds__(THREADS)
                     pass2_twiddle_table<R1, R2, false>(v, tw, oj);
                     cl::Dft<R2, false>::run(v);
 #pragma unroll
-                    for (int s = 0; s < R2; ++s) acc[s] = c_add(acc[s], c_mul(v[s], Sr[R1 * s]));
+                    for (int s = 0; s < R2; ++s) acc[s] = c_add(acc[s], c_mul(v[s], ld_hint(Sr + R1 * s, pol_s)));
                 }
             }
         }
@@ -368,6 +443,7 @@ __global__ void __launch_bounds__(THREADS)
     const bool owner = t < COLS * R1;
     const int oc = owner ? t / R1 : 0, oj = owner ? t - oc * R1 : 0;
     const int okx = kx0 + oc;
+    const uint64_t pol_s = policy_evict_first(), pol_a = policy_evict_last();
     if (t < COLS * LSTEP) {
         const int c = t / LSTEP, l = t - c * LSTEP;
         const int kx = kx0 + c, rn = r_begin + l;
@@ -410,7 +486,7 @@ __global__ void __launch_bounds__(THREADS)
                     const C *Sr = S + ((size_t)okx * nz + rl) * N + oj;
                     C v[R2];
 #pragma unroll
-                    for (int s = 0; s < R2; ++s) v[s] = c_mulc(dh[s], Sr[R1 * s]);
+                    for (int s = 0; s < R2; ++s) v[s] = c_mulc(dh[s], ld_hint(Sr + R1 * s, pol_s));
                     pass1_store<R2, true>(v, ex + (oc * LSTEP + l) * EXM, oj);
                 }
             }
@@ -431,7 +507,7 @@ __global__ void __launch_bounds__(THREADS)
 #pragma unroll
             for (int s = 0; s < R1; ++s) {
                 const int q = j + R2 * s;
-                if (q < ny) o[q] = v[s];
+                if (q < ny) st_hint(o + q, v[s], pol_a);
             }
         }
         __syncthreads();
