@@ -9,6 +9,7 @@
 #include <new>
 #include <string>
 
+#include "gm_fast_ops.h"
 #include "gm_plan.h"
 
 namespace {
@@ -204,8 +205,17 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
     g.nyp = (g.ny + 15) / 16 * 16;  // intermediate column pitch: whole 128-byte lines per column
     p->Nx = g.sx + g.nx - 1;
     p->Ny = g.sy + g.ny - 1;
-    g.NPx = gm_fft_length(p->Nx);
-    g.NPy = gm_fft_length(p->Ny);
+    // FFT lengths: the smallest lengths >= Nx, Ny that the register-codelet kernels are built for
+    // when both are within 25% of the smallest even 7-smooth lengths; otherwise those 7-smooth
+    // lengths (generic kernels).  Any length >= N gives the same products (Sec. 3).
+    {
+        const int sx7 = gm_fft_length(p->Nx), sy7 = gm_fft_length(p->Ny);
+        const int lx = fast_disabled() ? 0 : gm::fast_ladder_length(p->Nx, false);
+        const int ly = fast_disabled() ? 0 : gm::fast_ladder_length(p->Ny, true);
+        const bool ladder = lx && ly && 4 * lx <= 5 * sx7 && 4 * ly <= 5 * sy7;
+        g.NPx = ladder ? lx : sx7;
+        g.NPy = ladder ? ly : sy7;
+    }
     g.Kx = g.NPx / 2 + 1;
     p->dx = prm->dx; p->dy = prm->dy;
     p->zplanes.resize(g.nz + 1);

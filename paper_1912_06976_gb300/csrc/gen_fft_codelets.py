@@ -30,11 +30,11 @@ def cos2pi(k, n):
 def sin2pi(k, n):
     return float(mpmath.sin(2 * mpmath.pi * k / n))
 
-SIZES = [2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 20, 21, 24, 25, 27, 28, 32, 35]
+SIZES = [2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 18, 20, 21, 24, 25, 27, 28, 32, 35]
 
 # preferred split of composite sizes (N1, N2)
 SPLITS = {6: (2, 3), 8: (2, 4), 9: (3, 3), 10: (2, 5), 12: (4, 3), 14: (2, 7), 15: (3, 5), 16: (4, 4),
-          20: (4, 5), 21: (3, 7), 24: (8, 3), 25: (5, 5), 27: (3, 9), 28: (4, 7), 32: (4, 8), 35: (5, 7)}
+          18: (2, 9), 20: (4, 5), 21: (3, 7), 24: (8, 3), 25: (5, 5), 27: (3, 9), 28: (4, 7), 32: (4, 8), 35: (5, 7)}
 
 
 def lit(x):
