@@ -7,6 +7,7 @@ GPU many times over), FP32 apply, FP64 set-up excluded from the timing as the
 paper excludes FFTW planning (Sec. 5, Remark).  Prints one JSON line.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py --table1        # the size sweep of Sec. 5, Table 1 (one JSON line per size)
 
 N > 1 (launched by torch.distributed.run): every rank runs an independent
 replica on its own GPU (the operator has no exchange step on one GPU's data);
@@ -34,8 +35,9 @@ WORKLOAD = "grav300"
 METRIC = "G·m and G^T·d applies/s (FP32 vs FP64 on GPU) at rel err ≤1e-5; % HBM roofline"
 UNIT = "applies/s"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_1912_06976_gb300/csrc/apply.cu", "paper_1912_06976_gb300/csrc/gm_kernels.cuh",
-                  "paper_1912_06976_gb300/csrc/gm_common.cuh"]
+KERNEL_SOURCES = ["paper_1912_06976_gb300/csrc/gm_fast.cuh", "paper_1912_06976_gb300/csrc/gm_fast_impl.cuh",
+                  "paper_1912_06976_gb300/csrc/gm_fft_codelets.cuh", "paper_1912_06976_gb300/csrc/gm_common.cuh",
+                  "paper_1912_06976_gb300/csrc/apply_fast.cu"]
 
 
 def parse_args(argv=None):
@@ -47,6 +49,8 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--table1", action="store_true", help="run the Table 1 size sweep instead")
+    ap.add_argument("--table1-k", default="1-12", help="sizes k of the sweep, e.g. 1-12 or 3,6,12")
     return ap.parse_args(argv)
 
 
@@ -428,8 +432,134 @@ def run_ours(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- Table 1 sweep
+def table1_workloads(ks):
+    """Sec. 5, Table 1: s_x = 25 k, s_y = 15 k, n_z = 2 k (k = 1..12), without padding and with 5 %
+    of the stations per side rounded half up (the n column of Table 1: 918 = 27 x 17 x 2 for k = 1,
+    7616 = 56 x 34 x 4 for k = 2).  The table gives no cell size: 25 m cubes here."""
+    from paper_1912_06976_gb300 import workloads as W
+
+    out = []
+    for k in ks:
+        for pad in (0.0, 0.05):
+            sx, sy, nz = 25 * k, 15 * k, 2 * k
+            px, py = int(pad * sx + 0.5), int(pad * sy + 0.5)
+            out.append((k, pad, W.Workload(f"t1_k{k}_p{int(pad * 100)}", W.GRAVITY, sx, sy, nz, 25.0, 25.0, 25.0,
+                                           px, py)))
+    return out
+
+
+def cpu_fft_apply(spec, nz, ny, nx, sy, sx, m, d, workers):
+    """The host-CPU FFT baseline: the same algorithm as the GPU path with scipy.fft on all host
+    cores, using the library's spectra spec[kx][r][ky] (batched R2C over the layers, the depth
+    multiply-accumulate, one inverse for G m; one forward and n_z inverses for G^T d)."""
+    import numpy as np
+    import scipy.fft as sf
+
+    Kx, _, NPy = spec.shape
+    NPx = 2 * (Kx - 1)
+    S = np.ascontiguousarray(np.transpose(spec, (1, 2, 0)))  # [r][ky][kx]
+    x = np.zeros((nz, NPy, NPx), dtype=m.dtype)
+    x[:, :ny, :nx] = m
+    M = sf.rfft2(x, workers=workers)
+    D = np.einsum("rij,rij->ij", S, M)
+    fwd = sf.irfft2(D, s=(NPy, NPx), workers=workers)[:sy, :sx]
+    y = np.zeros((NPy, NPx), dtype=d.dtype)
+    y[:sy, :sx] = d
+    Dh = sf.rfft2(y, workers=workers)
+    tr = sf.irfft2(np.conj(S) * Dh[None], s=(NPy, NPx), workers=workers)[:, :ny, :nx]
+    return fwd, tr
+
+
+def run_table1(args):
+    """For every Table 1 size: GPU FP32 / FP64 applies per second (CUDA graph of forward +
+    transpose steps, L2 flushed between steps), the error against the oracle at sampled stations
+    and cells, the host-CPU FFT baseline and the dense oracle's rate on the host cores."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    from paper_1912_06976_gb300 import gravmag as gm
+    from paper_1912_06976_gb300 import workloads as W
+
+    if "-" in args.table1_k:
+        a, b = (int(v) for v in args.table1_k.split("-"))
+        ks = list(range(a, b + 1))
+    else:
+        ks = [int(v) for v in args.table1_k.split(",")]
+    workers = os.cpu_count() or 1
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for k, pad, w in table1_workloads(ks):
+        geom = O.Geometry(w.sx, w.sy, w.nz, w.dx, w.dy, w.zplanes, w.pxl, w.pxr, w.pyl, w.pyr, w.kind,
+                          w.incl_deg, w.decl_deg, w.F_nT)
+        m_np = W.gaussian_random_field(np.random.default_rng(k), w.model_shape, 4.0, 0.2)
+        d_np = W.random_vector(w.data_shape, k)
+        row = {"table1_k": k, "padding": pad, "stations": [w.sx, w.sy], "nz": w.nz, "cells": w.n}
+        rng = np.random.default_rng(100 + k)
+        st = np.sort(rng.choice(w.m, size=min(64, w.m), replace=False))
+        ce = np.sort(rng.choice(w.n, size=64, replace=False))
+        ref_f = O.forward(geom, m_np, stations=st)
+        ref_t = O.transpose(geom, d_np, cells=ce)
+        for prec, dt, name in ((gm.F32, torch.float32, "fp32"), (gm.F64, torch.float64, "fp64")):
+            op = gm.Operator.from_workload(w, precision=prec)
+            m = torch.as_tensor(m_np, dtype=dt, device="cuda").contiguous()
+            d = torch.as_tensor(d_np, dtype=dt, device="cuda").contiguous()
+            outd = torch.empty(op.data_shape, dtype=dt, device="cuda")
+            outm = torch.empty(op.model_shape, dtype=dt, device="cuda")
+            time_steps(op, m, d, outd, outm, flush, 3)
+            steps = 20
+            cap = capture_steps(op, m, d, outd, outm, flush, steps)
+            if cap is not None:
+                g, starts, ends = cap
+                g.replay()
+                torch.cuda.synchronize()
+                g.replay()
+                torch.cuda.synchronize()
+                per = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+            else:
+                per = time_steps(op, m, d, outd, outm, flush, steps)
+            op.forward(m, out=outd)
+            op.transpose(d, out=outm)
+            torch.cuda.synchronize()
+            f = outd.double().cpu().numpy()
+            t = outm.double().cpu().numpy()
+            inf = op.info
+            row[name] = {"applies_per_s": 2 * steps / (sum(per) / 1e3), "ms_per_apply": sum(per) / (2 * steps),
+                         "rel_err_forward": gm.rel_err(f.ravel()[st], ref_f),
+                         "rel_err_transpose": gm.rel_err(t.ravel()[ce], ref_t),
+                         "fft": [inf.fft_nx, inf.fft_ny], "path": "codelet" if inf.fft_nx in (
+                             32, 48, 64, 80, 96, 112, 128, 140, 160, 192, 224, 256, 288, 320, 384, 448, 512, 560, 576,
+                             640, 672, 768, 896, 1024) else "generic", "setup_ms": inf.setup_ms}
+            # host-CPU FFT baseline on the same spectra and inputs, same precision
+            spec = op.spectrum()
+            npdt = np.float64 if prec == gm.F64 else np.float32
+            mm, dd = m_np.astype(npdt), d_np.astype(npdt)
+            cpu_fft_apply(spec, w.nz, w.ny, w.nx, w.sy, w.sx, mm, dd, workers)
+            reps, t0 = 0, time.perf_counter()
+            while reps < 3 or time.perf_counter() - t0 < 1.0:
+                cf, ct = cpu_fft_apply(spec, w.nz, w.ny, w.nx, w.sy, w.sx, mm, dd, workers)
+                reps += 1
+            cpu_s = (time.perf_counter() - t0) / reps
+            row[name]["cpu_fft"] = {"applies_per_s": 2 / cpu_s, "cores": workers,
+                                    "rel_err_vs_gpu": max(gm.rel_err(cf, f), gm.rel_err(ct, t))}
+            op.close()
+        # dense oracle: sampled columns of G^T d, scaled to m * n entries per product
+        cells, t_or = 0, 0.0
+        while t_or < 1.0:
+            idx = rng.choice(w.n, size=O.threads(), replace=False)
+            t0 = time.perf_counter()
+            O.transpose(geom, d_np, idx)
+            t_or += time.perf_counter() - t0
+            cells += len(idx)
+        row["oracle_dense"] = {"applies_per_s": 1.0 / (t_or / (cells * w.m) * w.m * w.n), "cores": O.threads()}
+        print(json.dumps(row), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.table1:
+        return run_table1(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

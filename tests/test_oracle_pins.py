@@ -366,3 +366,22 @@ def test_table1_sizes_reproduce_with_per_side_padding():
         assert geom.m == m
         assert sx * sy * nz == n0
         assert _five_sig(geom.n) == n5
+
+
+def test_bench_table1_sweep_uses_the_table1_geometries():
+    """bench.py --table1 builds exactly the sizes of Table 1 (same fixture, same padding rule)."""
+    import os
+    import sys
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_sizes.txt")
+    rows = {r[0]: r for r in (list(map(int, ln.split())) for ln in open(path) if ln.strip() and not ln.startswith("#"))}
+    seen = set()
+    for k, pad, w in bench.table1_workloads(range(1, 13)):
+        _, sx, sy, nz, m, n0, n5 = rows[k]
+        assert (w.sx, w.sy, w.nz, w.m) == (sx, sy, nz, m)
+        assert (w.n if pad == 0 else _five_sig(w.n)) == (n0 if pad == 0 else n5)
+        seen.add((k, pad))
+    assert len(seen) == 24
