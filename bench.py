@@ -341,7 +341,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel: algorithmic bytes per launch / its mean launch time
     w_el = 4
-    spec_bytes = 2 * w_el * inf.nz * inf.fft_ny * inf.spec_nx
+    spec_bytes = inf.spectrum_bytes  # as stored: complex, or real even (a quarter) for gravity
     alg = {"fwd_rows_r2c": w_el * inf.n_model, "fwd_cols_mac": spec_bytes, "fwd_cols_inv": 0,
            "fwd_rows_c2r": w_el * inf.n_data, "tr_rows_r2c": w_el * inf.n_data, "tr_cols": spec_bytes,
            "tr_rows_c2r": w_el * inf.n_model}
@@ -353,6 +353,7 @@ def run_ours(args):
     apply_bytes = w_el * (inf.n_model + inf.n_data) + spec_bytes  # per forward or transpose product
     step_ms = t_ms / args.steps
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "spectrum_form": "real even (quarter)" if inf.spectrum_real else "complex",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                 "traffic": traffic, "algorithmic_bytes_per_launch": alg[dom],
                 "kernel_ms_per_launch": dom_ms,

@@ -134,14 +134,19 @@ typedef struct {
     size_t spectrum_bytes;   /* resident spectra                                          */
     size_t workspace_bytes;  /* resident workspace (intermediates + host-call staging)    */
     double setup_ms;         /* device time of the set-up kernels                         */
+    int spectrum_real;       /* 1: stored spectra are the real even spectra of the
+                                station-centred generator (gravity, equal padding on both
+                                sides), a quarter of the complex bytes; 0: complex        */
 } gm_info;
 
 GM_API gm_status gm_get_info(gm_handle h, gm_info *out);
 
-/* Copies the stored spectra to host memory: out holds spec_nx * nz * fft_ny
- * complex values (interleaved re, im) in the handle's precision, ordered
- * [kx][r][ky], i.e. the 2-D FFT of layer r's circulant generator at
- * frequency (kx, ky).  bytes must be at least spectrum_bytes. */
+/* Copies the spectra to host memory: out holds spec_nx * nz * fft_ny complex
+ * values (interleaved re, im) in the handle's precision, ordered [kx][r][ky],
+ * i.e. the 2-D FFT of layer r's circulant generator at frequency (kx, ky).
+ * bytes must be at least that size (2 * element size * spec_nx * nz * fft_ny).
+ * A handle that stores real even spectra (gm_info.spectrum_real) expands them
+ * on the host into this same complex form. */
 GM_API gm_status gm_copy_spectrum(gm_handle h, void *host_out, size_t bytes);
 
 /* Smallest even integer >= max(n, 2) whose prime factors are all in

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "gm_fast_ops.h"
 #include "gm_plan.h"
@@ -136,6 +137,26 @@ static void free_plan(gm_plan *p) {
     delete p;
 }
 
+template <typename R>
+void expand_real_spectrum(const gm_plan *h, const R *E, R *out) {
+    // T[kx][r][ky] = w(kx, ky) E[kx][r][min(ky, N'y - ky)], w = exp(+2 pi i (pxl kx / N'x + pyl ky / N'y))
+    const gm::Geo &g = h->geo;
+    const int H = g.NPy / 2 + 1;
+    for (int kx = 0; kx < g.Kx; ++kx)
+        for (int ky = 0; ky < g.NPy; ++ky) {
+            const double ph = 2.0 * kPi *
+                              ((double)(((long long)g.pxl * kx) % g.NPx) / g.NPx +
+                               (double)(((long long)g.pyl * ky) % g.NPy) / g.NPy);
+            const double wr = std::cos(ph), wi = std::sin(ph);
+            for (int r = 0; r < g.nz; ++r) {
+                const double e = (double)E[((size_t)kx * g.nz + r) * H + (ky <= g.NPy / 2 ? ky : g.NPy - ky)];
+                R *o = out + 2 * (((size_t)kx * g.nz + r) * g.NPy + ky);
+                o[0] = (R)(wr * e);
+                o[1] = (R)(wi * e);
+            }
+        }
+}
+
 extern "C" {
 
 int gm_fft_length(int n) {
@@ -249,6 +270,14 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
     const size_t small = cel * (size_t)g.Kx * g.sy;
     const size_t n_model = (size_t)g.nx * g.ny * g.nz, n_data = (size_t)g.sx * g.sy;
     p->fast = !fast_disabled() && gm::fast_path_supported(g.NPx, g.NPy);
+    // gravity with the same padding on both sides: real even spectra, a quarter of the bytes
+    // (register-codelet path; GM_COMPLEX_SPECTRA=1 keeps the complex form)
+    {
+        const char *cs = std::getenv("GM_COMPLEX_SPECTRA");
+        p->spec_real = p->fast && p->kind == GM_GRAVITY && g.pxl == p->pxr && g.pyl == p->pyr &&
+                       !(cs && cs[0] && cs[0] != '0');
+    }
+    if (p->spec_real) p->spec_bytes = rel * (size_t)g.Kx * g.nz * (g.NPy / 2 + 1);
     size_t part = 0, ncount = 0;
     if (p->fast) {
         gm::fast_plan_groups(p);
@@ -415,15 +444,29 @@ gm_status gm_get_info(gm_handle h, gm_info *out) {
     out->spectrum_bytes = h->spec_bytes;
     out->workspace_bytes = h->work_bytes;
     out->setup_ms = h->setup_ms;
+    out->spectrum_real = h->spec_real ? 1 : 0;
     return ok();
 }
 
 gm_status gm_copy_spectrum(gm_handle h, void *host_out, size_t bytes) {
     if (!h || !host_out) return fail(GM_EINVAL, "NULL argument");
-    if (bytes < h->spec_bytes) return fail(GM_EINVAL, "buffer smaller than spectrum_bytes");
+    const gm::Geo &g = h->geo;
+    const size_t el = h->precision == GM_F64 ? sizeof(double) : sizeof(float);
+    const size_t need = 2 * el * (size_t)g.Kx * g.nz * g.NPy;
+    if (bytes < need) return fail(GM_EINVAL, "buffer smaller than spec_nx * nz * fft_ny complex values");
     DeviceGuard dg(h->device);
-    cudaError_t e = cudaMemcpy(host_out, h->spec, h->spec_bytes, cudaMemcpyDeviceToHost);
+    if (!h->spec_real) {
+        cudaError_t e = cudaMemcpy(host_out, h->spec, h->spec_bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "copy spectrum");
+        return ok();
+    }
+    std::vector<unsigned char> tmp(h->spec_bytes);
+    cudaError_t e = cudaMemcpy(tmp.data(), h->spec, h->spec_bytes, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "copy spectrum");
+    if (h->precision == GM_F64)
+        expand_real_spectrum<double>(h, reinterpret_cast<const double *>(tmp.data()), static_cast<double *>(host_out));
+    else
+        expand_real_spectrum<float>(h, reinterpret_cast<const float *>(tmp.data()), static_cast<float *>(host_out));
     return ok();
 }
 

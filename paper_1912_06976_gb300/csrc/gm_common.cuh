@@ -10,6 +10,11 @@
 
 namespace gm {
 
+template <typename C> struct real_of;
+template <> struct real_of<float2> { using type = float; };
+template <> struct real_of<double2> { using type = double; };
+
+
 // Complex type of a real precision.
 template <typename R> struct cpx_of;
 template <> struct cpx_of<float> { using type = float2; };

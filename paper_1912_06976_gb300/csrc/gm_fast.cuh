@@ -85,6 +85,29 @@ __device__ __forceinline__ void discard_line(const void *p) {
     asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
 }
 
+// Real even spectra (gravity, symmetric padding): the stored spectrum of layer r is the real
+// E_r(kx, ky) (ky <= N/2, even in ky) of the station-centred generator, and the spectrum of the
+// embedded generator is T_r = w * E_r with the separable phase
+//   w(kx, ky) = exp(+2 pi i (pxl kx / NX + pyl ky / N)) = conj(twx[pxl kx mod NX]) conj(tw[pyl ky mod N]),
+// tw / twx the tables exp(-2 pi i e / N).  w is the same for every layer, so the forward applies it
+// once to the depth sum and the transpose applies conj(w) once to the data transform.
+// Multiplies v[s] (s < R2, frequency ky = j + R1 s) by w(kx, ky), or by conj(w) when CONJ; the
+// ky exponent advances by pyl R1 mod N per s (all products stay below 2^31 for N, NX <= 4096).
+template <int R1, int R2, bool CONJ, typename C>
+__device__ __forceinline__ void apply_phase(C (&v)[R2], const C *__restrict__ twx, int NX, int pxl, int kx,
+                                            const C *tw, int N, int pyl, int j) {
+    const C wx = c_conj(twx[(pxl * kx) % NX]);
+    int e = (pyl * j) % N;
+    const int de = (pyl * R1) % N;
+#pragma unroll
+    for (int s = 0; s < R2; ++s) {
+        const C w = c_mul(wx, c_conj(tw[e]));
+        v[s] = c_mul(v[s], CONJ ? c_conj(w) : w);
+        e += de;
+        if (e >= N) e -= N;
+    }
+}
+
 template <int R1, bool INV, typename C>
 __device__ __forceinline__ void pass1_store(C (&v)[R1], C *ex, int j) {
     cl::Dft<R1, INV>::run(v);
@@ -336,7 +359,8 @@ template <typename C, int R1, int R2, int COLS, int LSTEP, int THREADS>
 __global__ void __launch_bounds__(THREADS)
     k_cols_fwd_mac(const C *__restrict__ A, const C *__restrict__ S, C *__restrict__ part, C *__restrict__ B,
                    unsigned int *__restrict__ counters, int Kx, int nz, int ny, int nyp, int sy,
-                   int layers_per_group, int ngroups, const C *__restrict__ twg) {
+                   int layers_per_group, int ngroups, const C *__restrict__ twg, int spec_real, int pxl, int pyl,
+                   const C *__restrict__ twx) {
     constexpr int N = R1 * R2, EX = Ex<R1, R2>::value;
     static_assert(COLS * R1 <= THREADS, "one pass-2 owner per thread");
     extern __shared__ unsigned char smem_raw[];
@@ -386,19 +410,34 @@ __global__ void __launch_bounds__(THREADS)
             for (int l = 0; l < LSTEP; ++l) {
                 const int rl = r + l;
                 if (rl < r_end) {
-                    const C *Sr = S + ((size_t)okx * nz + rl) * N + oj;
                     C v[R2];
                     pass2_gather<R1, R2>(v, ex + (oc * LSTEP + l) * EX, oj);
                     pass2_twiddle_table<R1, R2, false>(v, tw, oj);
                     cl::Dft<R2, false>::run(v);
+                    if (spec_real) {
+                        using Rr = typename real_of<C>::type;
+                        const Rr *Er = reinterpret_cast<const Rr *>(S) + ((size_t)okx * nz + rl) * (N / 2 + 1);
 #pragma unroll
-                    for (int s = 0; s < R2; ++s) acc[s] = c_add(acc[s], c_mul(v[s], ld_hint(Sr + R1 * s, pol_s)));
+                        for (int s = 0; s < R2; ++s) {
+                            const int ky = oj + R1 * s;
+                            const Rr e = ld_hint(Er + (ky <= N / 2 ? ky : N - ky), pol_s);
+                            acc[s].x += v[s].x * e;
+                            acc[s].y += v[s].y * e;
+                        }
+                    } else {
+                        const C *Sr = S + ((size_t)okx * nz + rl) * N + oj;
+#pragma unroll
+                        for (int s = 0; s < R2; ++s)
+                            acc[s] = c_add(acc[s], c_mul(v[s], ld_hint(Sr + R1 * s, pol_s)));
+                    }
                 }
             }
         }
         __syncthreads();
     }
     if (owner && okx < Kx) {
+        if (spec_real)  // the phase of the embedded generator, once for the whole depth sum
+            apply_phase<R1, R2, false>(acc, twx, 2 * (Kx - 1), pxl, okx, tw, N, pyl, oj);
         C *o = part + ((size_t)g * Kx + okx) * N + oj;
 #pragma unroll
         for (int s = 0; s < R2; ++s) o[R1 * s] = acc[s];
@@ -426,7 +465,8 @@ __global__ void __launch_bounds__(THREADS)
 template <typename C, int R1, int R2, int COLS, int LSTEP, int THREADS>
 __global__ void __launch_bounds__(THREADS)
     k_cols_tr(const C *__restrict__ D1, const C *__restrict__ S, C *__restrict__ A2, int Kx, int nz, int ny, int nyp,
-              int sy, int layers_per_group, const C *__restrict__ twg) {
+              int sy, int layers_per_group, const C *__restrict__ twg, int spec_real, int pxl, int pyl,
+              const C *__restrict__ twx) {
     constexpr int N = R1 * R2;
     constexpr int EXF = Ex<R1, R2>::value;  // forward exchange (pass-1 radix R1)
     constexpr int EXI = Ex<R2, R1>::value;  // inverse exchange (pass-1 radix R2)
@@ -447,7 +487,8 @@ __global__ void __launch_bounds__(THREADS)
     if (t < COLS * LSTEP) {
         const int c = t / LSTEP, l = t - c * LSTEP;
         const int kx = kx0 + c, rn = r_begin + l;
-        if (kx < Kx && rn < r_end) prefetch_l2(S + ((size_t)kx * nz + rn) * N, (unsigned int)(sizeof(C) * N));
+        if (kx < Kx && rn < r_end && !spec_real)
+            prefetch_l2(S + ((size_t)kx * nz + rn) * N, (unsigned int)(sizeof(C) * N));
     }
     load_table<N, THREADS>(tw, twg);
     // forward transform of the data columns: pass 1 items j < R2 take D1[kx][j + R2*rr]
@@ -469,13 +510,16 @@ __global__ void __launch_bounds__(THREADS)
         pass2_gather<R1, R2>(dh, ex + oc * EXM, oj);
         pass2_twiddle_table<R1, R2, false>(dh, tw, oj);
         cl::Dft<R2, false>::run(dh);
+        if (spec_real && okx < Kx)  // conj(T_r) Dh = E_r (conj(w) Dh): conj(w) once for all layers
+            apply_phase<R1, R2, true>(dh, twx, 2 * (Kx - 1), pxl, okx, tw, N, pyl, oj);
     }
     __syncthreads();
     for (int r = r_begin; r < r_end; r += LSTEP) {
         if (t < COLS * LSTEP) {
             const int c = t / LSTEP, l = t - c * LSTEP;
             const int kx = kx0 + c, rn = r + LSTEP + l;
-            if (kx < Kx && rn < r_end) prefetch_l2(S + ((size_t)kx * nz + rn) * N, (unsigned int)(sizeof(C) * N));
+            if (kx < Kx && rn < r_end && !spec_real)
+                prefetch_l2(S + ((size_t)kx * nz + rn) * N, (unsigned int)(sizeof(C) * N));
         }
         // inverse pass 1 (radix R2) by the owners: y[oj + R1*rr] = conj(S) * Dh, rr < R2
         if (owner && okx < Kx) {
@@ -483,10 +527,21 @@ __global__ void __launch_bounds__(THREADS)
             for (int l = 0; l < LSTEP; ++l) {
                 const int rl = r + l;
                 if (rl < r_end) {
-                    const C *Sr = S + ((size_t)okx * nz + rl) * N + oj;
                     C v[R2];
+                    if (spec_real) {
+                        using Rr = typename real_of<C>::type;
+                        const Rr *Er = reinterpret_cast<const Rr *>(S) + ((size_t)okx * nz + rl) * (N / 2 + 1);
 #pragma unroll
-                    for (int s = 0; s < R2; ++s) v[s] = c_mulc(dh[s], ld_hint(Sr + R1 * s, pol_s));
+                        for (int s = 0; s < R2; ++s) {
+                            const int ky = oj + R1 * s;
+                            const Rr e = ld_hint(Er + (ky <= N / 2 ? ky : N - ky), pol_s);
+                            v[s] = c_make<C>(dh[s].x * e, dh[s].y * e);
+                        }
+                    } else {
+                        const C *Sr = S + ((size_t)okx * nz + rl) * N + oj;
+#pragma unroll
+                        for (int s = 0; s < R2; ++s) v[s] = c_mulc(dh[s], ld_hint(Sr + R1 * s, pol_s));
+                    }
                     pass1_store<R2, true>(v, ex + (oc * LSTEP + l) * EXM, oj);
                 }
             }

@@ -120,12 +120,14 @@ cudaError_t cols_fwd_mac(const gm_plan *p, const cpx_t<R> *A, const cpx_t<R> *S,
     const Geo &g = p->geo;
     const size_t sm = fwd_mac_smem<R, Y1, Y2>(g.nyp);
     auto k = reinterpret_cast<void (*)(const C *, const C *, C *, C *, unsigned int *, int, int, int, int, int, int,
-                                       int, const C *)>(const_cast<void *>(fwd_kernel<R, Y1, Y2>()));
+                                       int, const C *, int, int, int, const C *)>(
+        const_cast<void *>(fwd_kernel<R, Y1, Y2>()));
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
     dim3 grd((g.Kx + COLS - 1) / COLS, p->fast_groups_fwd);
     k<<<grd, T, sm, s>>>(A, S, part, B, static_cast<unsigned int *>(p->work_counters), g.Kx, g.nz, g.ny, g.nyp,
-                         g.sy, p->fast_lpg_fwd, p->fast_groups_fwd, static_cast<const C *>(p->tw_y));
+                         g.sy, p->fast_lpg_fwd, p->fast_groups_fwd, static_cast<const C *>(p->tw_y),
+                         p->spec_real ? 1 : 0, g.pxl, g.pyl, static_cast<const C *>(p->tw_x));
     return cudaGetLastError();
 }
 
@@ -136,12 +138,13 @@ cudaError_t cols_tr(const gm_plan *p, const cpx_t<R> *D1, const cpx_t<R> *S, cpx
     constexpr int COLS = CC::COLS_TR, T = CC::T_TR;
     const Geo &g = p->geo;
     const size_t sm = tr_smem<R, Y1, Y2>();
-    auto k = reinterpret_cast<void (*)(const C *, const C *, C *, int, int, int, int, int, int, const C *)>(
-        const_cast<void *>(tr_kernel<R, Y1, Y2>()));
+    auto k = reinterpret_cast<void (*)(const C *, const C *, C *, int, int, int, int, int, int, const C *, int, int,
+                                       int, const C *)>(const_cast<void *>(tr_kernel<R, Y1, Y2>()));
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
     dim3 grd((g.Kx + COLS - 1) / COLS, p->fast_groups_tr);
-    k<<<grd, T, sm, s>>>(D1, S, A2, g.Kx, g.nz, g.ny, g.nyp, g.sy, p->fast_lpg_tr, static_cast<const C *>(p->tw_y));
+    k<<<grd, T, sm, s>>>(D1, S, A2, g.Kx, g.nz, g.ny, g.nyp, g.sy, p->fast_lpg_tr, static_cast<const C *>(p->tw_y),
+                         p->spec_real ? 1 : 0, g.pxl, g.pyl, static_cast<const C *>(p->tw_x));
     return cudaGetLastError();
 }
 

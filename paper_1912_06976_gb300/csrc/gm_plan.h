@@ -25,9 +25,11 @@ struct gm_plan {
     gm::FftDesc fx{}, fy{};
     void *tw_x = nullptr, *tw_y = nullptr;
 
-    // Spectra [Kx][nz][NPy], complex in the apply precision.
+    // Spectra [Kx][nz][NPy], complex in the apply precision; or, with spec_real, the real even
+    // spectra of the station-centred generator, [Kx][nz][NPy/2 + 1] (see build_spectra).
     void *spec = nullptr;
     size_t spec_bytes = 0;
+    bool spec_real = false;
 
     // Workspace: the large intermediate (forward [Kx][nz][ny], transpose [nz][ny][Kx]),
     // the small one (forward [sy][Kx], transpose [Kx][sy]) and host-call staging.

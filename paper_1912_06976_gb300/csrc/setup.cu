@@ -18,6 +18,7 @@
 //     Tcircpaddedgeneral), zeros elsewhere.
 //  K3 2-D FFT of each generator in FP64 (rows, then columns), then rounding
 //     to the apply precision.
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -120,6 +121,44 @@ __global__ void k_round_to_f32(const double2 *__restrict__ in, float2 *__restric
         if (e_ != cudaSuccess) { err = e_; goto done; } \
     } while (0)
 
+// Real even spectra of the station-centred generator (gravity with symmetric padding, Sec. 3,
+// Eq. Tcircpadded): the generator e_r(dx, dy) = k_r(dx, dy) stored at (dx mod N'x, dy mod N'y) is
+// the embedded generator t_r reflected and shifted by the padding, e[j] = t[(-j - pxl) mod N'], so
+// E_r = w conj(T_r) with w = exp(+2 pi i (pxl kx / N'x + pyl ky / N'y)).  The gravity kernel is
+// even in both offsets and the padding is the same on both sides, so E_r is real and even in ky:
+// E[kx][r][ky] for ky <= N'y/2 is kept.  dev[0] / dev[1] receive the largest |Im| and the largest
+// ky-mirror mismatch, and dev[2] the largest |E|, as the bit patterns of non-negative doubles.
+template <typename Rout>
+__global__ void k_real_even_spectrum(const double2 *__restrict__ S64, Rout *__restrict__ E, int Kx, int nz, int NPx,
+                                     int NPy, int pxl, int pyl, unsigned long long *__restrict__ dev) {
+    const int H = NPy / 2 + 1;
+    const size_t total = (size_t)Kx * nz * H;
+    double mi = 0, mm = 0, me = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int ky = (int)(i % H);
+        const size_t kr = i / H;  // kx * nz + r
+        const int kx = (int)(kr / nz);
+        auto e_at = [&](int kyy) {
+            double sx_, cx_, sy_, cy_;
+            sincospi(2.0 * (double)(((long long)pxl * kx) % NPx) / NPx, &sx_, &cx_);
+            sincospi(2.0 * (double)(((long long)pyl * kyy) % NPy) / NPy, &sy_, &cy_);
+            const double wr = cx_ * cy_ - sx_ * sy_, wi = sx_ * cy_ + cx_ * sy_;
+            const double2 t = S64[kr * NPy + kyy];
+            // w * conj(t)
+            return make_double2(wr * t.x + wi * t.y, wi * t.x - wr * t.y);
+        };
+        const double2 e = e_at(ky);
+        const double2 f = e_at(ky == 0 ? 0 : NPy - ky);
+        mi = fmax(mi, fmax(fabs(e.y), fabs(f.y)));
+        mm = fmax(mm, fabs(e.x - f.x));
+        me = fmax(me, fabs(e.x));
+        E[i] = (Rout)e.x;
+    }
+    atomicMax(dev + 0, (unsigned long long)__double_as_longlong(mi));
+    atomicMax(dev + 1, (unsigned long long)__double_as_longlong(mm));
+    atomicMax(dev + 2, (unsigned long long)__double_as_longlong(me));
+}
+
 cudaError_t build_spectra(gm_plan *p, cudaStream_t s) {
     const Geo &g = p->geo;
     const int ncx = p->Nx + 1, ncy = p->Ny + 1;
@@ -176,7 +215,30 @@ cudaError_t build_spectra(gm_plan *p, cudaStream_t s) {
         k_cols_fft<double2><<<grd2, 256, sm2, s>>>(S64, g.nz, g.NPy, fy64);
         GM_TRY(cudaGetLastError());
     }
-    if (p->precision == GM_F64) {
+    if (p->spec_real) {
+        unsigned long long *dev = nullptr;
+        unsigned long long hostv[3] = {0, 0, 0};
+        GM_TRY(cudaMalloc(&dev, sizeof(hostv)));
+        GM_TRY(cudaMemsetAsync(dev, 0, sizeof(hostv), s));
+        if (p->precision == GM_F64)
+            k_real_even_spectrum<double><<<1024, 256, 0, s>>>(S64, static_cast<double *>(p->spec), g.Kx, g.nz, g.NPx,
+                                                              g.NPy, g.pxl, g.pyl, dev);
+        else
+            k_real_even_spectrum<float><<<1024, 256, 0, s>>>(S64, static_cast<float *>(p->spec), g.Kx, g.nz, g.NPx,
+                                                             g.NPy, g.pxl, g.pyl, dev);
+        err = cudaGetLastError();
+        if (err == cudaSuccess) err = cudaMemcpyAsync(hostv, dev, sizeof(hostv), cudaMemcpyDeviceToHost, s);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+        cudaFree(dev);
+        GM_TRY(err);
+        double v[3];
+        std::memcpy(v, hostv, sizeof(v));
+        // exact arithmetic makes Im and the mirror mismatch zero; FP64 rounding leaves ~1e-16 |E|
+        if (!(v[0] <= 1e-9 * v[2]) || !(v[1] <= 1e-9 * v[2])) {
+            err = cudaErrorInvalidValue;
+            goto done;
+        }
+    } else if (p->precision == GM_F64) {
         GM_TRY(cudaMemcpyAsync(p->spec, S64, sizeof(double2) * nspec, cudaMemcpyDeviceToDevice, s));
     } else {
         k_round_to_f32<<<1024, 256, 0, s>>>(S64, reinterpret_cast<float2 *>(p->spec), nspec);

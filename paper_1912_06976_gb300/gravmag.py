@@ -59,7 +59,7 @@ class Info(ctypes.Structure):
         ("kind", ctypes.c_int), ("precision", ctypes.c_int),
         ("n_model", ctypes.c_int64), ("n_data", ctypes.c_int64),
         ("spectrum_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
-        ("setup_ms", ctypes.c_double),
+        ("setup_ms", ctypes.c_double), ("spectrum_real", ctypes.c_int),
     ]
 
 

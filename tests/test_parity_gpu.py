@@ -229,6 +229,60 @@ def test_codelet_path_matches_generic_path(gm, name, prec, monkeypatch):
     ref_f, ref_t = run(gm, w, prec, m, d)
     monkeypatch.delenv("GM_GENERIC_FFT")
     got_f, got_t = run(gm, w, prec, m, d)
-    tol = 1e-13 if prec == 1 else 2e-6
+    # FP64: the bound of the oracle gate (the 300x250x60 transpose is 8e-13 from the oracle itself)
+    tol = 1e-12 if prec == 1 else 2e-6
     assert rel_err(got_f, ref_f) < tol
     assert rel_err(got_t, ref_t) < tol
+
+
+def test_gravity_real_spectra_are_the_fft_of_the_oracle_generator(gm):
+    """Gravity with equal padding on both sides stores the real even spectra of the
+    station-centred generator (a quarter of the bytes); expanded with the padding phase they are
+    numpy's 2-D FFT of the embedded generator built from oracle entries (Eq. Tcircpadded)."""
+    w = W.Workload("gsym", W.GRAVITY, 14, 12, 3, 20.0, 30.0, 10.0, 2, 2)  # 32 x 32: codelet lengths
+    geom = geometry(w)
+    op = gm.Operator.from_workload(w, precision=gm.F64)
+    inf = op.info
+    assert inf.spectrum_real == 1
+    assert inf.spectrum_bytes == 8 * inf.spec_nx * inf.nz * (inf.fft_ny // 2 + 1)
+    S = op.spectrum()
+    Nx, Ny = inf.fft_nx, inf.fft_ny
+    T = np.zeros((w.nz, Ny, Nx))
+    for r in range(w.nz):
+        for v in range(-(w.ny - 1), w.sy):
+            j = max(v, 0)
+            for u in range(-(w.nx - 1), w.sx):
+                i = max(u, 0)
+                T[r, v % Ny, u % Nx] = O.entry(geom, i, j, i - u, j - v, r)
+    assert rel_err(np.transpose(S, (1, 2, 0)), np.fft.rfft2(T)) < 1e-12
+    op.close()
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("name", ["grav16", "grav300", "grav64"])
+def test_gravity_real_spectra_match_complex_spectra(gm, monkeypatch, name, prec):
+    """The real-spectrum path (one real x complex product per layer and the padding phase once)
+    against the complex-spectrum path of the same kernels (GM_COMPLEX_SPECTRA=1), whole vectors."""
+    w = W.WORKLOADS[name]
+    m = W.model(name, 0) if name != "grav64" else W.random_vector(w.model_shape, 3)
+    d = W.data(name, 0) if name != "grav64" else W.random_vector(w.data_shape, 4)
+    monkeypatch.setenv("GM_COMPLEX_SPECTRA", "1")
+    ref_f, ref_t = run(gm, w, prec, m, d)
+    monkeypatch.delenv("GM_COMPLEX_SPECTRA")
+    op = gm.Operator.from_workload(w, precision=prec)
+    assert op.info.spectrum_real == 1
+    op.close()
+    got_f, got_t = run(gm, w, prec, m, d)
+    # FP64: the bound of the oracle gate (the 300x250x60 transpose is 8e-13 from the oracle itself)
+    tol = 1e-12 if prec == 1 else 2e-6
+    assert rel_err(got_f, ref_f) < tol
+    assert rel_err(got_t, ref_t) < tol
+
+
+def test_asymmetric_padding_and_magnetic_keep_complex_spectra(gm):
+    for w in (W.Workload("gasym", W.GRAVITY, 11, 9, 3, 20.0, 30.0, 10.0, 2, 3, 90.0, 0.0, 50000.0, 1, 3),
+              W.WORKLOADS["mag64"]):
+        op = gm.Operator.from_workload(w, precision=gm.F32)
+        assert op.info.spectrum_real == 0
+        assert op.info.spectrum_bytes == 8 * op.info.spec_nx * op.info.nz * op.info.fft_ny
+        op.close()
