@@ -30,6 +30,14 @@ template <int R1, int R2> struct Ex {
     static constexpr int value = (raw % 2) ? raw : raw + 1;
 };
 
+// Programmatic dependent launch: the apply kernels are launched so that the next kernel on the
+// stream may start before this one ends.  pdl_wait() blocks until the preceding kernel has
+// completed and its memory is visible (a no-op for a normal launch); every kernel calls it before
+// its first access to data another kernel writes or reads.  pdl_trigger() lets the next kernel be
+// scheduled once every block of this one has passed it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Asks the memory system to bring `bytes` (a multiple of 16) at a 16-byte aligned global address
 // into L2; fire-and-forget, nothing waits on it.
 __device__ __forceinline__ void prefetch_l2(const void *p, unsigned int bytes) {
@@ -108,6 +116,20 @@ __device__ __forceinline__ void apply_phase(C (&v)[R2], const C *__restrict__ tw
     }
 }
 
+// Index of frequency ky = j + R1 s in a real even spectrum stored for ky <= N/2 (N = R1 R2): with
+// R2 even, s < R2/2 never passes N/2 and s >= R2/2 always maps to N - ky = R1 (R2 - s) - j, so
+// both halves are a lane base plus a compile-time offset.
+template <int R1, int R2>
+__device__ __forceinline__ int even_index(int j, int s) {
+    constexpr int N = R1 * R2;
+    if constexpr (R2 % 2 == 0) {
+        return s < R2 / 2 ? j + R1 * s : R1 * (R2 - s) - j;
+    } else {
+        const int ky = j + R1 * s;
+        return ky <= N / 2 ? ky : N - ky;
+    }
+}
+
 template <int R1, bool INV, typename C>
 __device__ __forceinline__ void pass1_store(C (&v)[R1], C *ex, int j) {
     cl::Dft<R1, INV>::run(v);
@@ -168,6 +190,7 @@ __global__ void __launch_bounds__(THREADS) k_rows_r2c(const Rin *__restrict__ in
     const uint64_t pol_in = policy_evict_first(), pol_out = policy_evict_last();
     // warp p transforms pair p on its own: both passes and the exchange stay inside the warp
     const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    pdl_wait();
     if (lane < R2) {
         const int p = wp, j = lane;
         const int qa = q0 + 2 * p;
@@ -199,6 +222,7 @@ __global__ void __launch_bounds__(THREADS) k_rows_r2c(const Rin *__restrict__ in
         for (int s = 0; s < R2; ++s) ex[p2 * EX + j2 + R1 * s] = v[s];  // natural order Z[k]
     }
     __syncthreads();  // the separation below reads every pair (coalesced stores across pairs)
+    pdl_trigger();
     // separate the two real rows: FFT(a)[k] = (Z[k] + conj Z[-k]) / 2, FFT(b)[k] = (Z[k] - conj Z[-k]) / 2i
 #pragma unroll 4
     for (int it = threadIdx.x; it < PAIRS * Kx; it += THREADS) {
@@ -236,6 +260,7 @@ __global__ void __launch_bounds__(THREADS) k_rows_c2r(const C *__restrict__ in, 
     C *ex = xs + 2 * PAIRS * Kx;               // [PAIRS][EX]
     const int q0 = blockIdx.x * 2 * PAIRS;
     const int layer = blockIdx.y;
+    pdl_wait();
     {
         // staging in one round: every load of a thread is issued before its shared-memory stores
         constexpr int TOT = Kx * 2 * PAIRS, BATCH = (TOT + THREADS - 1) / THREADS;
@@ -283,6 +308,7 @@ __global__ void __launch_bounds__(THREADS) k_rows_c2r(const C *__restrict__ in, 
         pass1_store<R1, true>(v, ex + p * EX, j);
     }
     __syncwarp();
+    pdl_trigger();
     const auto sc = (decltype(ex[0].x))scale;
     if (lane < R1) {
         const int p = wp, j = lane;
@@ -381,6 +407,7 @@ __global__ void __launch_bounds__(THREADS)
     const uint64_t pol_s = policy_evict_first();
     load_table<N, THREADS>(tw, twg);
     const int row_lines = (ny * (int)sizeof(C) + 127) / 128;  // lines of one A column (pitch nyp: whole lines)
+    pdl_wait();
     for (int r = r_begin; r < r_end; r += LSTEP) {
         for (int it = t; it < COLS * LSTEP * R2; it += THREADS) {
             const int c = it / (LSTEP * R2);
@@ -419,8 +446,7 @@ __global__ void __launch_bounds__(THREADS)
                         const Rr *Er = reinterpret_cast<const Rr *>(S) + ((size_t)okx * nz + rl) * (N / 2 + 1);
 #pragma unroll
                         for (int s = 0; s < R2; ++s) {
-                            const int ky = oj + R1 * s;
-                            const Rr e = ld_hint(Er + (ky <= N / 2 ? ky : N - ky), pol_s);
+                            const Rr e = ld_hint(Er + even_index<R1, R2>(oj, s), pol_s);
                             acc[s].x += v[s].x * e;
                             acc[s].y += v[s].y * e;
                         }
@@ -435,6 +461,7 @@ __global__ void __launch_bounds__(THREADS)
         }
         __syncthreads();
     }
+    pdl_trigger();
     if (owner && okx < Kx) {
         if (spec_real)  // the phase of the embedded generator, once for the whole depth sum
             apply_phase<R1, R2, false>(acc, twx, 2 * (Kx - 1), pxl, okx, tw, N, pyl, oj);
@@ -491,6 +518,7 @@ __global__ void __launch_bounds__(THREADS)
             prefetch_l2(S + ((size_t)kx * nz + rn) * N, (unsigned int)(sizeof(C) * N));
     }
     load_table<N, THREADS>(tw, twg);
+    pdl_wait();
     // forward transform of the data columns: pass 1 items j < R2 take D1[kx][j + R2*rr]
     for (int it = t; it < COLS * R2; it += THREADS) {
         const int c = it / R2, j = it - c * R2;
@@ -533,8 +561,7 @@ __global__ void __launch_bounds__(THREADS)
                         const Rr *Er = reinterpret_cast<const Rr *>(S) + ((size_t)okx * nz + rl) * (N / 2 + 1);
 #pragma unroll
                         for (int s = 0; s < R2; ++s) {
-                            const int ky = oj + R1 * s;
-                            const Rr e = ld_hint(Er + (ky <= N / 2 ? ky : N - ky), pol_s);
+                            const Rr e = ld_hint(Er + even_index<R1, R2>(oj, s), pol_s);
                             v[s] = c_make<C>(dh[s].x * e, dh[s].y * e);
                         }
                     } else {
@@ -567,6 +594,7 @@ __global__ void __launch_bounds__(THREADS)
         }
         __syncthreads();
     }
+    pdl_trigger();
 }
 
 }  // namespace fast

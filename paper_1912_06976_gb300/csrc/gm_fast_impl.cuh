@@ -14,6 +14,22 @@
 namespace gm {
 namespace {
 
+// Launch with programmatic stream serialisation (see pdl_wait / pdl_trigger in gm_fast.cuh).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 constexpr int kPairs = 8;   // two-row transforms per row-kernel CTA (many rows)
 constexpr int kLstep = 2;   // layers per step in the column kernels
 
@@ -34,7 +50,8 @@ cudaError_t rows_r2c_p(const R *in, int rows, int row_len, int nlayers, cpx_t<R>
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
     dim3 grd((rows + 2 * PAIRS - 1) / (2 * PAIRS), nlayers);
-    k<<<grd, THREADS, sm, s>>>(in, rows, row_len, nlayers, out, out_rows, static_cast<const C *>(tw));
+    e = launch_pdl(k, grd, dim3(THREADS), sm, s, in, rows, row_len, nlayers, out, out_rows, static_cast<const C *>(tw));
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -64,8 +81,9 @@ cudaError_t rows_c2r_p(const cpx_t<R> *in, long long ld_k, long long ld_layer, l
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
     dim3 grd((rows + 2 * PAIRS - 1) / (2 * PAIRS), nlayers);
-    k<<<grd, THREADS, sm, s>>>(in, ld_k, ld_layer, ld_row, rows, out, row_len_out, scale,
-                               static_cast<const C *>(tw), disc);
+    e = launch_pdl(k, grd, dim3(THREADS), sm, s, in, ld_k, ld_layer, ld_row, rows, out, row_len_out, scale,
+                   static_cast<const C *>(tw), disc);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -125,9 +143,10 @@ cudaError_t cols_fwd_mac(const gm_plan *p, const cpx_t<R> *A, const cpx_t<R> *S,
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
     dim3 grd((g.Kx + COLS - 1) / COLS, p->fast_groups_fwd);
-    k<<<grd, T, sm, s>>>(A, S, part, B, static_cast<unsigned int *>(p->work_counters), g.Kx, g.nz, g.ny, g.nyp,
-                         g.sy, p->fast_lpg_fwd, p->fast_groups_fwd, static_cast<const C *>(p->tw_y),
-                         p->spec_real ? 1 : 0, g.pxl, g.pyl, static_cast<const C *>(p->tw_x));
+    e = launch_pdl(k, grd, dim3(T), sm, s, A, S, part, B, static_cast<unsigned int *>(p->work_counters), g.Kx, g.nz,
+                   g.ny, g.nyp, g.sy, p->fast_lpg_fwd, p->fast_groups_fwd, static_cast<const C *>(p->tw_y),
+                   p->spec_real ? 1 : 0, g.pxl, g.pyl, static_cast<const C *>(p->tw_x));
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -143,8 +162,10 @@ cudaError_t cols_tr(const gm_plan *p, const cpx_t<R> *D1, const cpx_t<R> *S, cpx
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
     dim3 grd((g.Kx + COLS - 1) / COLS, p->fast_groups_tr);
-    k<<<grd, T, sm, s>>>(D1, S, A2, g.Kx, g.nz, g.ny, g.nyp, g.sy, p->fast_lpg_tr, static_cast<const C *>(p->tw_y),
-                         p->spec_real ? 1 : 0, g.pxl, g.pyl, static_cast<const C *>(p->tw_x));
+    e = launch_pdl(k, grd, dim3(T), sm, s, D1, S, A2, g.Kx, g.nz, g.ny, g.nyp, g.sy, p->fast_lpg_tr,
+                   static_cast<const C *>(p->tw_y), p->spec_real ? 1 : 0, g.pxl, g.pyl,
+                   static_cast<const C *>(p->tw_x));
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
