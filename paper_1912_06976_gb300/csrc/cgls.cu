@@ -48,6 +48,8 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 // part[blk] = partial SUM a[i]^2 (i < na); part[kRedBlocks + blk] = partial SUM b[i]^2 (i < nb)
 template <typename R>
 __global__ void k_sumsq2(const R *__restrict__ a, size_t na, const R *__restrict__ b, size_t nb, double *part) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh[32];
     double sa = 0, sb = 0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < na; i += (size_t)gridDim.x * blockDim.x)
@@ -71,6 +73,8 @@ __device__ double sum_parts(const double *part, double *sh) {
 // init: gamma = ||s||^2 (parts[0..]); resid[0] = sqrt(||r||^2) (parts[K..]);
 // converged once gamma <= tol2 * gamma_0
 __global__ void k_init_scalars(const double *part, double *sc, double *resid, double alpha2, double tol2) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh[32];
     double s2 = sum_parts(part, sh);
     double r2 = sum_parts(part + kRedBlocks, sh);
@@ -85,6 +89,8 @@ __global__ void k_init_scalars(const double *part, double *sc, double *resid, do
 
 // a = gamma / (||q||^2 + alpha^2 ||p||^2), or 0 once converged
 __global__ void k_step_length(const double *part, double *sc) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh[32];
     double q2 = sum_parts(part, sh);
     double p2 = sum_parts(part + kRedBlocks, sh);
@@ -97,6 +103,8 @@ __global__ void k_step_length(const double *part, double *sc) {
 
 // b = gamma' / gamma (0 once converged), gamma = gamma'; resid[k] = ||r||
 __global__ void k_beta(const double *part, double *sc, double *resid, int k) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh[32];
     double s2 = sum_parts(part, sh);
     double r2 = sum_parts(part + kRedBlocks, sh);
@@ -117,6 +125,8 @@ template <typename R> constexpr double cgls_tol2() {
 // r = d - r (r holds G x0 on entry)
 template <typename R>
 __global__ void k_residual0(const R *__restrict__ d, R *__restrict__ r, size_t m) {
+    pdl_wait();
+    pdl_trigger();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
         r[i] = d[i] - r[i];
 }
@@ -124,6 +134,8 @@ __global__ void k_residual0(const R *__restrict__ d, R *__restrict__ r, size_t m
 // s -= alpha^2 x; p = s (when set_p)
 template <typename R>
 __global__ void k_s_update(R *__restrict__ s, const R *__restrict__ x, R *__restrict__ p, size_t n, R a2, int set_p) {
+    pdl_wait();
+    pdl_trigger();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         R v = s[i] - a2 * x[i];
         s[i] = v;
@@ -135,6 +147,8 @@ __global__ void k_s_update(R *__restrict__ s, const R *__restrict__ x, R *__rest
 template <typename R>
 __global__ void k_update_xr(R *__restrict__ x, const R *__restrict__ p, size_t n, R *__restrict__ r,
                             const R *__restrict__ q, size_t m, const double *sc) {
+    pdl_wait();
+    pdl_trigger();
     const R a = (R)sc[S_A];
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         x[i] += a * p[i];
@@ -145,6 +159,8 @@ __global__ void k_update_xr(R *__restrict__ x, const R *__restrict__ p, size_t n
 // p = s + b p
 template <typename R>
 __global__ void k_update_p(R *__restrict__ p, const R *__restrict__ s, size_t n, const double *sc) {
+    pdl_wait();
+    pdl_trigger();
     const R b = (R)sc[S_B];
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         p[i] = s[i] + b * p[i];
@@ -189,29 +205,29 @@ static cudaError_t cgls_t(gm_plan *p, const R *d, const R *x0, R *x, double alph
         CG_TRY(launch_forward(p, x, r, st, &l));  // r = G x0
         launches += l;
     }
-    k_residual0<R><<<vb, vt, 0, st>>>(d, r, m);
+    launch_pdl(k_residual0<R>, dim3(vb), dim3(vt), 0, st, d, r, m);
     {
         int l = 0;
         CG_TRY(launch_transpose(p, r, s, st, &l));  // s = G^T r
         launches += l;
     }
-    k_s_update<R><<<vb, vt, 0, st>>>(s, x, pv, n, (R)(alpha * alpha), 1);
-    k_sumsq2<R><<<vb, vt, 0, st>>>(s, n, r, m, part);
-    k_init_scalars<<<1, 1024, 0, st>>>(part, sc, resid, alpha * alpha, cgls_tol2<R>());
+    launch_pdl(k_s_update<R>, dim3(vb), dim3(vt), 0, st, s, x, pv, n, (R)(alpha * alpha), 1);
+    launch_pdl(k_sumsq2<R>, dim3(vb), dim3(vt), 0, st, s, n, r, m, part);
+    launch_pdl(k_init_scalars, dim3(1), dim3(1024), 0, st, part, sc, resid, alpha * alpha, cgls_tol2<R>());
     launches += 4;
     for (k = 1; k <= iters; ++k) {
         int l = 0;
         CG_TRY(launch_forward(p, pv, q, st, &l));  // q = G p
         launches += l;
-        k_sumsq2<R><<<vb, vt, 0, st>>>(q, m, pv, n, part);
-        k_step_length<<<1, 1024, 0, st>>>(part, sc);
-        k_update_xr<R><<<vb, vt, 0, st>>>(x, pv, n, r, q, m, sc);
+        launch_pdl(k_sumsq2<R>, dim3(vb), dim3(vt), 0, st, q, m, pv, n, part);
+        launch_pdl(k_step_length, dim3(1), dim3(1024), 0, st, part, sc);
+        launch_pdl(k_update_xr<R>, dim3(vb), dim3(vt), 0, st, x, pv, n, r, q, m, sc);
         CG_TRY(launch_transpose(p, r, s, st, &l));  // s = G^T r
         launches += l;
-        k_s_update<R><<<vb, vt, 0, st>>>(s, x, pv, n, (R)(alpha * alpha), 0);
-        k_sumsq2<R><<<vb, vt, 0, st>>>(s, n, r, m, part);
-        k_beta<<<1, 1024, 0, st>>>(part, sc, resid, k);
-        k_update_p<R><<<vb, vt, 0, st>>>(pv, s, n, sc);
+        launch_pdl(k_s_update<R>, dim3(vb), dim3(vt), 0, st, s, x, pv, n, (R)(alpha * alpha), 0);
+        launch_pdl(k_sumsq2<R>, dim3(vb), dim3(vt), 0, st, s, n, r, m, part);
+        launch_pdl(k_beta, dim3(1), dim3(1024), 0, st, part, sc, resid, k);
+        launch_pdl(k_update_p<R>, dim3(vb), dim3(vt), 0, st, pv, s, n, sc);
         launches += 6;
         CG_TRY(cudaGetLastError());
     }
@@ -296,29 +312,29 @@ static cudaError_t cgls_noalloc_t(gm_plan *p, const R *d, const R *x0, R *x, dou
         NA_TRY(launch_forward(p, x, r, st, &l));
         launches += l;
     }
-    k_residual0<R><<<vb, vt, 0, st>>>(d, r, m);
+    launch_pdl(k_residual0<R>, dim3(vb), dim3(vt), 0, st, d, r, m);
     {
         int l = 0;
         NA_TRY(launch_transpose(p, r, s, st, &l));
         launches += l;
     }
-    k_s_update<R><<<vb, vt, 0, st>>>(s, x, pv, n, (R)(alpha * alpha), 1);
-    k_sumsq2<R><<<vb, vt, 0, st>>>(s, n, r, m, part);
-    k_init_scalars<<<1, 1024, 0, st>>>(part, sc, resid, alpha * alpha, cgls_tol2<R>());
+    launch_pdl(k_s_update<R>, dim3(vb), dim3(vt), 0, st, s, x, pv, n, (R)(alpha * alpha), 1);
+    launch_pdl(k_sumsq2<R>, dim3(vb), dim3(vt), 0, st, s, n, r, m, part);
+    launch_pdl(k_init_scalars, dim3(1), dim3(1024), 0, st, part, sc, resid, alpha * alpha, cgls_tol2<R>());
     launches += 4;
     for (k = 1; k <= iters; ++k) {
         int l = 0;
         NA_TRY(launch_forward(p, pv, q, st, &l));
         launches += l;
-        k_sumsq2<R><<<vb, vt, 0, st>>>(q, m, pv, n, part);
-        k_step_length<<<1, 1024, 0, st>>>(part, sc);
-        k_update_xr<R><<<vb, vt, 0, st>>>(x, pv, n, r, q, m, sc);
+        launch_pdl(k_sumsq2<R>, dim3(vb), dim3(vt), 0, st, q, m, pv, n, part);
+        launch_pdl(k_step_length, dim3(1), dim3(1024), 0, st, part, sc);
+        launch_pdl(k_update_xr<R>, dim3(vb), dim3(vt), 0, st, x, pv, n, r, q, m, sc);
         NA_TRY(launch_transpose(p, r, s, st, &l));
         launches += l;
-        k_s_update<R><<<vb, vt, 0, st>>>(s, x, pv, n, (R)(alpha * alpha), 0);
-        k_sumsq2<R><<<vb, vt, 0, st>>>(s, n, r, m, part);
-        k_beta<<<1, 1024, 0, st>>>(part, sc, resid, k);
-        k_update_p<R><<<vb, vt, 0, st>>>(pv, s, n, sc);
+        launch_pdl(k_s_update<R>, dim3(vb), dim3(vt), 0, st, s, x, pv, n, (R)(alpha * alpha), 0);
+        launch_pdl(k_sumsq2<R>, dim3(vb), dim3(vt), 0, st, s, n, r, m, part);
+        launch_pdl(k_beta, dim3(1), dim3(1024), 0, st, part, sc, resid, k);
+        launch_pdl(k_update_p<R>, dim3(vb), dim3(vt), 0, st, pv, s, n, sc);
         launches += 6;
         NA_TRY(cudaGetLastError());
     }

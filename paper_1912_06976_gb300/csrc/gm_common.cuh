@@ -10,6 +10,30 @@
 
 namespace gm {
 
+// Programmatic dependent launch: kernels launched with launch_pdl may start before the previous
+// kernel on the stream has finished.  pdl_wait() blocks until that kernel has completed and its
+// memory is visible (a no-op under a normal launch); a kernel calls it before its first access to
+// data another kernel writes or reads.  pdl_trigger() lets the next kernel be scheduled once every
+// block of this one has passed it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 template <typename C> struct real_of;
 template <> struct real_of<float2> { using type = float; };
 template <> struct real_of<double2> { using type = double; };

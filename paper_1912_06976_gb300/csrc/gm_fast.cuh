@@ -30,14 +30,6 @@ template <int R1, int R2> struct Ex {
     static constexpr int value = (raw % 2) ? raw : raw + 1;
 };
 
-// Programmatic dependent launch: the apply kernels are launched so that the next kernel on the
-// stream may start before this one ends.  pdl_wait() blocks until the preceding kernel has
-// completed and its memory is visible (a no-op for a normal launch); every kernel calls it before
-// its first access to data another kernel writes or reads.  pdl_trigger() lets the next kernel be
-// scheduled once every block of this one has passed it.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 // Asks the memory system to bring `bytes` (a multiple of 16) at a 16-byte aligned global address
 // into L2; fire-and-forget, nothing waits on it.
 __device__ __forceinline__ void prefetch_l2(const void *p, unsigned int bytes) {

@@ -14,22 +14,6 @@
 namespace gm {
 namespace {
 
-// Launch with programmatic stream serialisation (see pdl_wait / pdl_trigger in gm_fast.cuh).
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
-}
-
 constexpr int kPairs = 8;   // two-row transforms per row-kernel CTA (many rows)
 constexpr int kLstep = 2;   // layers per step in the column kernels
 
