@@ -35,6 +35,7 @@ WORKLOAD = "grav300"
 METRIC = "G·m and G^T·d applies/s (FP32 vs FP64 on GPU) at rel err ≤1e-5; % HBM roofline"
 UNIT = "applies/s"
 FALLBACK_HBM_GBS = 6800.0
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 KERNEL_SOURCES = ["paper_1912_06976_gb300/csrc/gm_fast.cuh", "paper_1912_06976_gb300/csrc/gm_fast_impl.cuh",
                   "paper_1912_06976_gb300/csrc/gm_fft_codelets.cuh", "paper_1912_06976_gb300/csrc/gm_common.cuh",
                   "paper_1912_06976_gb300/csrc/apply_fast.cu"]
@@ -363,6 +364,21 @@ def run_ours(args):
     traffic = profiled_traffic(dom, w.name)
     apply_bytes = w_el * (inf.n_model + inf.n_data) + spec_bytes  # per forward or transpose product
     step_ms = t_ms / args.steps
+    # ALU view of the same kernel: 5 N log2 N flops per complex transform of length N (the usual
+    # count), 4 flops per real x complex (8 per complex x complex) depth multiply-accumulate
+    import math
+
+    fx, fy, kx, nz = inf.fft_nx, inf.fft_ny, inf.spec_nx, inf.nz
+    tf_y = 5.0 * fy * math.log2(fy)
+    mac = (4.0 if inf.spectrum_real else 8.0) * kx * nz * fy
+    col_flops = {"fwd_cols_mac": kx * nz * tf_y + mac + kx * tf_y, "tr_cols": kx * tf_y + mac + kx * nz * tf_y}
+    if dom in col_flops:
+        alu = {"kernel": dom, "gflop_per_launch": col_flops[dom] / 1e9,
+               "achieved_tflops": col_flops[dom] / (dom_ms / 1e3) / 1e12, "peak_tflops": FP32_PEAK_TFLOPS,
+               "frac": col_flops[dom] / (dom_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+               "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+    else:
+        alu = None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "spectrum_form": "real even (quarter)" if inf.spectrum_real else "complex",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
@@ -370,7 +386,8 @@ def run_ours(args):
                 "kernel_ms_per_launch": dom_ms,
                 "apply_effective_gbs": 2 * apply_bytes / (step_ms / 1e3) / 1e9,
                 "apply_frac": 2 * apply_bytes / (step_ms / 1e3) / 1e9 / peak,
-                "kernel_share": {k: v[1] / sum(x[1] for x in ktimes.values()) for k, v in ktimes.items()}}
+                "kernel_share": {k: v[1] / sum(x[1] for x in ktimes.values()) for k, v in ktimes.items()},
+                "alu_view": alu}
 
     # end to end through the host-buffer entry points (pinned host memory, copies timed)
     mh = m.cpu().pin_memory()
