@@ -82,6 +82,8 @@ def _load():
         lib.gmo_entry.argtypes = [gp] + [ctypes.c_int] * 5
         lib.gmo_rows.restype = None
         lib.gmo_rows.argtypes = [gp, i64p, ctypes.c_int64, dp]
+        lib.gmo_entries.restype = None
+        lib.gmo_entries.argtypes = [gp, i64p, i64p, ctypes.c_int64, dp]
         lib.gmo_forward.restype = None
         lib.gmo_forward.argtypes = [gp, dp, i64p, ctypes.c_int64, dp]
         lib.gmo_transpose.restype = None
@@ -193,6 +195,17 @@ def rows(geom: Geometry, stations) -> np.ndarray:
     out = np.zeros((st.size, geom.n))
     g, _z = geom._c()
     _load().gmo_rows(ctypes.byref(g), _ip(st), st.size, _dp(out))
+    return out
+
+
+def entries(geom: Geometry, stations, cells) -> np.ndarray:
+    """G[stations[t], cells[t]] for each t (parallel over t)."""
+    st = np.ascontiguousarray(stations, dtype=np.int64)
+    cl = np.ascontiguousarray(cells, dtype=np.int64)
+    assert st.shape == cl.shape
+    out = np.zeros(st.size)
+    g, _z = geom._c()
+    _load().gmo_entries(ctypes.byref(g), _ip(st), _ip(cl), st.size, _dp(out))
     return out
 
 

@@ -210,6 +210,21 @@ void gmo_rows(const gmo_geom *g, const int64_t *rows, int64_t nrows, double *out
     }
 }
 
+/* Scattered entries: out[t] = G[stations[t], cells[t]] for t < n (stations k = j*sx + i, cells
+ * l = (r*ny + q)*nx + p); the unit of work of the oracle's products, for timing samples. */
+void gmo_entries(const gmo_geom *g, const int64_t *stations, const int64_t *cells, int64_t n, double *out) {
+    const int nx = gmo_nx(g), ny = gmo_ny(g);
+    ld mc[5] = {0, 0, 0, 0, 0};
+    if (g->kind == GMO_MAGNETIC) mag_coeffs(g, mc);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < n; ++t) {
+        const int i = (int)(stations[t] % g->sx), j = (int)(stations[t] / g->sx);
+        const int64_t l = cells[t];
+        const int p = (int)(l % nx), q = (int)((l / nx) % ny), r = (int)(l / ((int64_t)nx * ny));
+        out[t] = (double)entry_ld(g, mc, i, j, p, q, r);
+    }
+}
+
 /* d[k] = SUM_l G[k, l] m[l] for the stations listed in rows (all stations
  * when rows == NULL, in which case nrows must be sx*sy).  Sums in long double. */
 void gmo_forward(const gmo_geom *g, const double *m, const int64_t *rows, int64_t nrows,

@@ -385,3 +385,13 @@ def test_bench_table1_sweep_uses_the_table1_geometries():
         assert (w.n if pad == 0 else _five_sig(w.n)) == (n0 if pad == 0 else n5)
         seen.add((k, pad))
     assert len(seen) == 24
+
+
+def test_scattered_entries_match_dense_rows():
+    """entries() (the timing sample unit) returns exactly the dense matrix's entries."""
+    geom = O.Geometry.uniform(5, 4, 3, 10.0, 12.0, 8.0, 1, 2, O.MAGNETIC, 60.0, 15.0)
+    G = O.dense(geom)
+    rng = np.random.default_rng(5)
+    st = rng.integers(0, geom.m, 200)
+    ce = rng.integers(0, geom.n, 200)
+    assert np.array_equal(O.entries(geom, st, ce), G[st, ce])
