@@ -113,10 +113,13 @@ GM_API gm_status apply_forward(gm_handle h, const void *m_dev, void *d_dev, void
  * generator is real).  d_dev: m elements, m_dev: n elements, overwritten. */
 GM_API gm_status apply_transpose(gm_handle h, const void *d_dev, void *m_dev, void *stream);
 
-/* The same products from and to HOST buffers: copies the input to the
- * handle's device staging buffer, applies, copies the result back and
- * synchronises the stream before returning.  Pinned host memory makes the
- * copies asynchronous DMA; pageable memory works too. */
+/* The same products from and to HOST buffers; they synchronise the stream
+ * before returning.  When both buffers are page-locked (cudaHostAlloc /
+ * cudaHostRegister, e.g. torch pin_memory) the kernels read the input and
+ * write the output in place through the GPU's view of host memory, with no
+ * copies; otherwise (or with GM_HOST_STAGING=1 in the environment) the input
+ * is copied to the handle's device staging buffer, the product runs there and
+ * the result is copied back.  Pageable memory works in the staged form. */
 GM_API gm_status apply_forward_host(gm_handle h, const void *m_host, void *d_host, void *stream);
 GM_API gm_status apply_transpose_host(gm_handle h, const void *d_host, void *m_host, void *stream);
 

@@ -395,6 +395,16 @@ gm_status apply_transpose(gm_handle h, const void *d_dev, void *m_dev, void *str
     return ok();
 }
 
+// Device address of a page-locked host buffer the GPU can access directly, or nullptr.
+static void *device_view_of_pinned(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 static gm_status host_apply(gm_handle h, const void *in_host, void *out_host, void *stream, bool fwd) {
     if (!h) return fail(GM_EINVAL, "handle is NULL");
     if (!in_host || !out_host) return fail(GM_EINVAL, "NULL buffer");
@@ -402,6 +412,20 @@ static gm_status host_apply(gm_handle h, const void *in_host, void *out_host, vo
     const size_t rel = h->precision == GM_F64 ? sizeof(double) : sizeof(float);
     const size_t n = (size_t)h->geo.nx * h->geo.ny * h->geo.nz, m = (size_t)h->geo.sx * h->geo.sy;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // Page-locked buffers are read and written in place by the kernels (over the host link), with
+    // no staging copies; GM_HOST_STAGING=1 forces the staged path.
+    const char *stg = std::getenv("GM_HOST_STAGING");
+    void *in_dev = device_view_of_pinned(in_host), *out_dev = device_view_of_pinned(out_host);
+    if (in_dev && out_dev && !(stg && stg[0] && stg[0] != '0')) {
+        int nl = 0;
+        cudaError_t e = fwd ? gm::launch_forward(h, in_dev, out_dev, s, &nl)
+                            : gm::launch_transpose(h, in_dev, out_dev, s, &nl);
+        h->last_launches = nl;
+        if (e != cudaSuccess) return cuda_fail(e, "apply");
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "synchronise");
+        return ok();
+    }
     void *din = fwd ? h->stage_m : h->stage_d, *dout = fwd ? h->stage_d : h->stage_m;
     const size_t nin = fwd ? n : m, nout = fwd ? m : n;
     cudaError_t e = cudaMemcpyAsync(din, in_host, rel * nin, cudaMemcpyHostToDevice, s);

@@ -286,3 +286,33 @@ def test_asymmetric_padding_and_magnetic_keep_complex_spectra(gm):
         assert op.info.spectrum_real == 0
         assert op.info.spectrum_bytes == 8 * op.info.spec_nx * op.info.nz * op.info.fft_ny
         op.close()
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_host_entry_points_direct_and_staged_agree(gm, monkeypatch, prec):
+    """Pinned buffers are used in place by the kernels; GM_HOST_STAGING=1 stages them through
+    device memory; pageable buffers are always staged.  All three give the device result."""
+    import torch
+
+    w = W.WORKLOADS["grav300"]
+    op = gm.Operator.from_workload(w, precision=prec)
+    dt = op.dtype
+    m = torch.as_tensor(W.model("grav300"), dtype=dt).contiguous()
+    d = torch.as_tensor(W.data("grav300"), dtype=dt).contiguous()
+    ref_d = op.forward(m.cuda()).cpu()
+    ref_m = op.transpose(d.cuda()).cpu()
+    outs = []
+    for pinned, staged in ((True, False), (True, True), (False, False)):
+        if staged:
+            monkeypatch.setenv("GM_HOST_STAGING", "1")
+        else:
+            monkeypatch.delenv("GM_HOST_STAGING", raising=False)
+        mi, di = (m.pin_memory(), d.pin_memory()) if pinned else (m.clone(), d.clone())
+        od = torch.empty(op.data_shape, dtype=dt)
+        om = torch.empty(op.model_shape, dtype=dt)
+        if pinned:
+            od, om = od.pin_memory(), om.pin_memory()
+        op.forward_host(mi, od)
+        op.transpose_host(di, om)
+        assert torch.equal(od, ref_d) and torch.equal(om, ref_m), (pinned, staged)
+    op.close()
