@@ -126,6 +126,19 @@ class Emitter:
             t2, t3 = self.add(x[1], x[3]), self.sub(x[1], x[3])
             it3 = self.mul_i(t3, sign)
             return [self.add(t0, t2), self.add(t1, it3), self.sub(t0, t2), self.sub(t1, it3)]
+        if n in SPLITS and math.gcd(*SPLITS[n]) == 1:
+            # prime-factor (Good-Thomas) form for coprime n1, n2: inputs at (n2 a + n1 b) mod n,
+            # DFT-n1 over a, DFT-n2 over b, output (k1, k2) at the CRT index
+            # k = (n2 (n2^-1 mod n1) k1 + n1 (n1^-1 mod n2) k2) mod n -- no twiddle factors
+            n1, n2 = SPLITS[n]
+            t1, t2 = pow(n2, -1, n1), pow(n1, -1, n2)
+            y = [self.dft([x[(n2 * a + n1 * b) % n] for a in range(n1)], sign) for b in range(n2)]
+            out = [None] * n
+            for k1 in range(n1):
+                row = self.dft([y[b][k1] for b in range(n2)], sign)
+                for k2 in range(n2):
+                    out[(n2 * t1 * k1 + n1 * t2 * k2) % n] = row[k2]
+            return out
         if n in SPLITS:
             n1, n2 = SPLITS[n]
             y = [[None] * n1 for _ in range(n2)]
