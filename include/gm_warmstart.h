@@ -9,7 +9,7 @@
  * padding) to a model m[16][S][S] of the same grid (16 depth layers), trained
  * on (model, G model + noise) pairs made with the forward product.  Its
  * prediction is the starting point x0 of gm_cgls; CGLS from x0 = 0 stays the
- * fallback and the judge of its error.
+ * fallback and the yardstick of its error.
  *
  * Architecture (tensors N x C x D x H x W, x fastest; every convolution has
  * kernel 3 in each convolved axis, "same" zero padding and a bias):

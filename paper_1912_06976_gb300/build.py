@@ -2,7 +2,7 @@
 
 Each .cu under csrc/ is compiled by nvcc for sm_103a only, in parallel, then
 linked into one shared library with the CUDA runtime linked statically, so the
-library depends on nothing but the driver.  Rebuilds only when a source or
+library depends on nothing but the CUDA driver.  Rebuilds only when a source or
 header is newer than the library.
 """
 from __future__ import annotations

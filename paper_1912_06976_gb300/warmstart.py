@@ -4,7 +4,7 @@ A convolutional network (2-D encoder, 3-D decoder; the architecture and its
 C ABI are in include/gm_warmstart.h) maps a data grid d[S][S] to a density
 model m[16][S][S].  It is trained on pairs (m, G m + 1% noise) whose data come
 from this library's FP32 forward product, and its prediction x0 = net(d)
-starts gm_cgls.  CGLS from x0 = 0 stays the fallback and the judge: the
+starts gm_cgls.  CGLS from x0 = 0 stays the fallback and the yardstick: the
 comparison reports the data misfit plain CGLS reaches and the iterations and
 G / G^T applies the warm-started CGLS needs to reach it.
 

@@ -1,4 +1,4 @@
-"""What the trained network gains over CGLS without it (the warm start's judge).
+"""What the trained network gains over CGLS without it (plain CGLS is the yardstick).
 
 A network trained on the GPU with the library's kernels (8,192 seeded pairs of the 64 x 64 x 16
 gravity grid, data from the FP32 forward product + 1 % noise, 3,000 Adam steps of batch 32) starts
