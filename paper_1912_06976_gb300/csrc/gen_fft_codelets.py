@@ -180,15 +180,155 @@ class Emitter:
         return out
 
 
+class CEmitter(Emitter):
+    """The same DFT algorithms, emitted as operations on whole complex values (type C) through the
+    cx_* helpers of the header prelude: one packed two-lane FP32 instruction per complex add,
+    subtract, real scaling or real multiply-add when C = float2 (scalar code for double2)."""
+
+    def let(self, expr):
+        t = self.tmp()
+        self.lines.append(f"const C {t} = {expr};")
+        return t
+
+    # complex values are names of C temporaries (or v[k]); None is an exact zero
+    def add(self, a, b):
+        if a is None:
+            return b
+        if b is None:
+            return a
+        return self.let(f"cx_add({a}, {b})")
+
+    def neg(self, a):
+        return None if a is None else self.let(f"cx_neg({a})")
+
+    def sub(self, a, b):
+        if b is None:
+            return a
+        if a is None:
+            return self.neg(b)
+        return self.let(f"cx_sub({a}, {b})")
+
+    def mul_i(self, a, sign):
+        if a is None:
+            return None
+        return self.let(f"cx_mul_i({a})" if sign > 0 else f"cx_mul_mi({a})")
+
+    def twiddle(self, a, k, n, sign):
+        if a is None:
+            return None
+        k %= n
+        if k == 0:
+            return a
+        if 4 * k == n:
+            return self.mul_i(a, sign)
+        if 2 * k == n:
+            return self.neg(a)
+        if 4 * k == 3 * n:
+            return self.mul_i(a, -sign)
+        c = cos2pi(k, n)
+        s = sign * sin2pi(k, n)
+        if 8 * k % n == 0:  # odd multiples of pi/4: |c| = |s|
+            mode = 1 if (c > 0) == (s > 0) else 0
+            return self.let(f"cx_rot_diag({a}, {lit(c)}, {lit(s)}, {mode})")
+        return self.let(f"cx_rot({a}, {lit(c)}, {lit(s)})")
+
+    def dft(self, x, sign):
+        n = len(x)
+        if n in (1, 2, 4) or n in SPLITS:
+            return Emitter.dft(self, x, sign)
+        # odd prime: symmetric pairs, linear combinations as multiply-add chains
+        h = (n - 1) // 2
+        a = [self.add(x[k], x[n - k]) for k in range(1, h + 1)]
+        b = [self.sub(x[k], x[n - k]) for k in range(1, h + 1)]
+
+        def lin(base, terms):
+            acc = base
+            for c, t in terms:
+                if t is None:
+                    continue
+                acc = self.let(f"cx_fma({t}, {lit(c)}, {acc})") if acc is not None else \
+                    self.let(f"cx_scale({t}, {lit(c)})")
+            return acc
+
+        out = [None] * n
+        acc = x[0]
+        for t in a:
+            acc = self.add(acc, t)
+        out[0] = acc
+        for m in range(1, h + 1):
+            A = lin(x[0], [(cos2pi(k * m, n), a[k - 1]) for k in range(1, h + 1)])
+            B = lin(None, [(sin2pi(k * m, n), b[k - 1]) for k in range(1, h + 1)])
+            # X_m = A + sign*i*B, X_{n-m} = A - sign*i*B
+            if B is None:
+                out[m] = out[n - m] = A
+            elif A is None:
+                out[m] = self.mul_i(B, sign)
+                out[n - m] = self.mul_i(B, -sign)
+            else:
+                out[m] = self.let(f"cx_addi({A}, {B}, {lit(float(sign))})")
+                out[n - m] = self.let(f"cx_subi({A}, {B}, {lit(float(sign))})")
+        return out
+
+
+PRELUDE = r"""
+// Complex helpers of the codelets: packed two-lane FP32 instructions for float2 (sm_100+), the
+// same operations lane by lane for double2.  Each lane rounds exactly as the scalar form would.
+__device__ __forceinline__ float2 cx_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 cx_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 cx_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 cx_mul_i(float2 a) { return make_float2(-a.y, a.x); }
+__device__ __forceinline__ float2 cx_mul_mi(float2 a) { return make_float2(a.y, -a.x); }
+__device__ __forceinline__ float2 cx_scale(float2 a, float c) { return __fmul2_rn(a, make_float2(c, c)); }
+__device__ __forceinline__ float2 cx_fma(float2 t, float c, float2 acc) { return __ffma2_rn(t, make_float2(c, c), acc); }
+__device__ __forceinline__ float2 cx_rot(float2 a, float c, float s) {
+    return __ffma2_rn(make_float2(a.y, a.x), make_float2(-s, s), __fmul2_rn(a, make_float2(c, c)));
+}
+// (x + i y)(c + i s) with |c| = |s|: mode 1 -> ((x - y) c, (x + y) s), mode 0 -> ((x + y) c, (x - y) s)
+__device__ __forceinline__ float2 cx_rot_diag(float2 a, float c, float s, int mode) {
+    const float2 u = __ffma2_rn(make_float2(a.y, a.y), mode ? make_float2(-1.f, 1.f) : make_float2(1.f, -1.f),
+                                make_float2(a.x, a.x));
+    return __fmul2_rn(u, make_float2(c, s));
+}
+// A + sign i B and A - sign i B
+__device__ __forceinline__ float2 cx_addi(float2 A, float2 B, float sign) {
+    return __ffma2_rn(make_float2(B.y, B.x), make_float2(-sign, sign), A);
+}
+__device__ __forceinline__ float2 cx_subi(float2 A, float2 B, float sign) {
+    return __ffma2_rn(make_float2(B.y, B.x), make_float2(sign, -sign), A);
+}
+
+__device__ __forceinline__ double2 cx_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cx_sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cx_neg(double2 a) { return make_double2(-a.x, -a.y); }
+__device__ __forceinline__ double2 cx_mul_i(double2 a) { return make_double2(-a.y, a.x); }
+__device__ __forceinline__ double2 cx_mul_mi(double2 a) { return make_double2(a.y, -a.x); }
+__device__ __forceinline__ double2 cx_scale(double2 a, double c) { return make_double2(a.x * c, a.y * c); }
+__device__ __forceinline__ double2 cx_fma(double2 t, double c, double2 acc) {
+    return make_double2(fma(t.x, c, acc.x), fma(t.y, c, acc.y));
+}
+__device__ __forceinline__ double2 cx_rot(double2 a, double c, double s) {
+    return make_double2(fma(-a.y, s, a.x * c), fma(a.x, s, a.y * c));
+}
+__device__ __forceinline__ double2 cx_rot_diag(double2 a, double c, double s, int mode) {
+    return mode ? make_double2((a.x - a.y) * c, (a.x + a.y) * s) : make_double2((a.x + a.y) * c, (a.x - a.y) * s);
+}
+__device__ __forceinline__ double2 cx_addi(double2 A, double2 B, double sign) {
+    return make_double2(fma(-sign, B.y, A.x), fma(sign, B.x, A.y));
+}
+__device__ __forceinline__ double2 cx_subi(double2 A, double2 B, double sign) {
+    return make_double2(fma(sign, B.y, A.x), fma(-sign, B.x, A.y));
+}
+"""
+
+
 def codelet(n, inverse, nin=None):
     """DFT-n on v[0..n-1]; with nin < n the inputs v[nin..n-1] are taken as zero (not read)."""
     nin = n if nin is None else nin
-    e = Emitter()
-    x = [(f"v[{k}].x", f"v[{k}].y") if k < nin else None for k in range(n)]
+    e = CEmitter()
+    x = [f"v[{k}]" if k < nin else None for k in range(n)]
     out = e.dft(x, +1 if inverse else -1)
     body = ["    " + ln for ln in e.lines]
-    body += [f"    v[{k}].x = {out[k][0] if out[k] else 'R(0)'};" for k in range(n)]
-    body += [f"    v[{k}].y = {out[k][1] if out[k] else 'R(0)'};" for k in range(n)]
+    body += [f"    v[{k}] = {out[k] if out[k] else 'C{}'};" for k in range(n)]
     name = ("idft" if inverse else "dft") + str(n) + ("" if nin == n else f"_in{nin}")
     return (f"template <typename C>\n__device__ __forceinline__ void {name}(C (&v)[{n}]) {{\n"
             f"    using R = decltype(v[0].x);\n" + "\n".join(body) + "\n}\n")
@@ -201,22 +341,31 @@ PRUNED = {}
 
 
 def selftest():
-    """Executes every emitted codelet body in Python and compares it with numpy's FFT."""
+    """Executes every emitted codelet body in Python (complex numbers standing in for C and the
+    cx_* helpers written out) and compares it with numpy's FFT."""
     import numpy as np
 
+    helpers = {
+        "cx_add": lambda a, b: a + b, "cx_sub": lambda a, b: a - b, "cx_neg": lambda a: -a,
+        "cx_mul_i": lambda a: 1j * a, "cx_mul_mi": lambda a: -1j * a, "cx_scale": lambda a, c: a * c,
+        "cx_fma": lambda t, c, acc: acc + c * t, "cx_rot": lambda a, c, s: a * complex(c, s),
+        "cx_rot_diag": lambda a, c, s, mode: (complex((a.real - a.imag) * c, (a.real + a.imag) * s) if mode
+                                              else complex((a.real + a.imag) * c, (a.real - a.imag) * s)),
+        "cx_addi": lambda A, B, sg: A + sg * 1j * B, "cx_subi": lambda A, B, sg: A - sg * 1j * B,
+    }
     rng = np.random.default_rng(0)
     worst = 0.0
     cases = [(n, n) for n in SIZES] + [(n, L) for n, ls in PRUNED.items() for L in ls]
     for n, nin in cases:
         for inv in (False, True):
-            e = Emitter()
-            out = e.dft([(f"vx[{k}]", f"vy[{k}]") if k < nin else None for k in range(n)], +1 if inv else -1)
-            code = [re.sub(r"R\(([^)]*)\)", r"\1", ln.replace("const R ", "")).rstrip(";") for ln in e.lines]
+            e = CEmitter()
+            out = e.dft([f"v[{k}]" if k < nin else None for k in range(n)], +1 if inv else -1)
+            code = [re.sub(r"R\(([^)]*)\)", r"\1", ln.replace("const C ", "")).rstrip(";") for ln in e.lines]
             x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
             x[nin:] = 0
-            env = {"vx": list(x.real), "vy": list(x.imag)}
+            env = dict(helpers, v=list(x))
             exec("\n".join(code), env)
-            got = np.array([(eval(o[0], env) + 1j * eval(o[1], env)) if o else 0j for o in out])
+            got = np.array([eval(o, env) if o else 0j for o in out])
             ref = np.fft.ifft(x) * n if inv else np.fft.fft(x)
             err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
             worst = max(worst, err)
@@ -228,7 +377,7 @@ def main():
     parts = ["// gm_fft_codelets.cuh -- GENERATED by gen_fft_codelets.py; do not edit by hand.",
              "// Straight-line in-register DFTs, natural order: dftN (forward, exp(-2 pi i nk/N)) and",
              "// idftN (inverse, exp(+2 pi i nk/N), unnormalised), for C = float2 or double2.",
-             "#pragma once", "", "namespace gm {", "namespace cl {", ""]
+             "#pragma once", "", "#include <cuda_runtime.h>", "", "namespace gm {", "namespace cl {", PRELUDE]
     for n in SIZES:
         parts.append(codelet(n, False))
         parts.append(codelet(n, True))
