@@ -30,6 +30,13 @@ template <int R1, int R2> struct Ex {
     static constexpr int value = (raw % 2) ? raw : raw + 1;
 };
 
+// Shared-memory region of one row pair in the c2r row kernel (radices R1, R2): the two staged
+// half spectra (2 (N/2 + 1) values) and, after them, the pair's exchange (Ex values) in place.
+template <int R1, int R2> struct C2rRegion {
+    static constexpr int staged = 2 * ((R1 * R2) / 2 + 1), ex = Ex<R1, R2>::value;
+    static constexpr int value = staged > ex ? staged : ex;
+};
+
 // Asks the memory system to bring `bytes` (a multiple of 16) at a 16-byte aligned global address
 // into L2; fire-and-forget, nothing waits on it.
 __device__ __forceinline__ void prefetch_l2(const void *p, unsigned int bytes) {
@@ -246,10 +253,11 @@ __global__ void __launch_bounds__(THREADS) k_rows_c2r(const C *__restrict__ in, 
                                                       long long ld_row, int rows, Rout *__restrict__ out,
                                                       int row_len_out, double scale, const C *__restrict__ tw,
                                                       int discard_in) {
-    constexpr int N = R1 * R2, EX = Ex<R1, R2>::value, Kx = N / 2 + 1, H = N / 2;
+    constexpr int N = R1 * R2, Kx = N / 2 + 1, H = N / 2, REG = C2rRegion<R1, R2>::value;
     extern __shared__ unsigned char smem_raw[];
-    C *xs = reinterpret_cast<C *>(smem_raw);  // [2*PAIRS][Kx]
-    C *ex = xs + 2 * PAIRS * Kx;               // [PAIRS][EX]
+    // region p (REG values) holds the staged rows 2p and 2p+1 ([0, Kx) and [Kx, 2Kx)) and later the
+    // exchange of pair p: only warp p reads those rows, so the two uses need no block barrier
+    C *const sm = reinterpret_cast<C *>(smem_raw);  // [PAIRS][REG]
     const int q0 = blockIdx.x * 2 * PAIRS;
     const int layer = blockIdx.y;
     pdl_wait();
@@ -269,7 +277,7 @@ __global__ void __launch_bounds__(THREADS) k_rows_c2r(const C *__restrict__ in, 
             const int it = threadIdx.x + b * THREADS;
             if (it < TOT) {
                 const int k = it / (2 * PAIRS), row = it - k * 2 * PAIRS;
-                xs[row * Kx + k] = tmp[b];
+                sm[(row >> 1) * REG + (row & 1) * Kx + k] = tmp[b];
             }
         }
     }
@@ -285,9 +293,10 @@ __global__ void __launch_bounds__(THREADS) k_rows_c2r(const C *__restrict__ in, 
             }
         }
     }
+    C *const ex = sm + wp * REG;  // this warp's pair: staged rows, then exchange
     if (lane < R2) {  // warp p runs both passes of pair p
-        const int p = wp, j = lane;
-        const C *x1r = xs + (2 * p) * Kx, *x2r = x1r + Kx;
+        const int j = lane;
+        const C *x1r = ex, *x2r = ex + Kx;
         C v[R1];
 #pragma unroll
         for (int rr = 0; rr < R1; ++rr) {
@@ -297,18 +306,19 @@ __global__ void __launch_bounds__(THREADS) k_rows_c2r(const C *__restrict__ in, 
             if (n > H) { a.y = -a.y; b.y = -b.y; }
             v[rr] = c_make<C>(a.x - b.y, a.y + b.x);  // X1 + i X2
         }
-        pass1_store<R1, true>(v, ex + p * EX, j);
+        __syncwarp(R2 >= 32 ? 0xffffffffu : ((1u << R2) - 1u));  // the pair's rows are in registers
+        pass1_store<R1, true>(v, ex, j);
     }
     __syncwarp();
     pdl_trigger();
     const auto sc = (decltype(ex[0].x))scale;
     if (lane < R1) {
-        const int p = wp, j = lane;
+        const int j = lane;
         C v[R2];
-        pass2_gather<R1, R2>(v, ex + p * EX, j);
+        pass2_gather<R1, R2>(v, ex, j);
         pass2_twiddle_table<R1, R2, true>(v, tw, j);
         cl::Dft<R2, true>::run(v);
-        const int qa = q0 + 2 * p;
+        const int qa = q0 + 2 * wp;
         Rout *oa = out + ((size_t)layer * rows + qa) * row_len_out;
 #pragma unroll
         for (int s = 0; s < R2; ++s) {

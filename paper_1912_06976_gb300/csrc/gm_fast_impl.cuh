@@ -60,7 +60,7 @@ cudaError_t rows_c2r_p(const cpx_t<R> *in, long long ld_k, long long ld_layer, l
                          ? 1
                          : 0;
     // inverse radices (X2, X1): pass-2 items j < X2 write X2-wide coalesced rows
-    const size_t sm = sizeof(C) * (2 * PAIRS * Kx + PAIRS * fast::Ex<X2, X1>::value);
+    const size_t sm = sizeof(C) * PAIRS * fast::C2rRegion<X2, X1>::value;
     auto k = fast::k_rows_c2r<C, R, X2, X1, PAIRS, THREADS>;
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
