@@ -19,7 +19,8 @@
  * Layouts (Eq. htilde, x fastest):
  *   model  m[r][q][p]  r < nz, q < ny, p < nx   (n = nx*ny*nz elements)
  *   data   d[j][i]     j < sy, i < sx           (m = sx*sy elements)
- * Element type: float for a GM_F32 handle, double for a GM_F64 handle.
+ * Element type: float for a GM_F32 handle, double for a GM_F64 or GM_DF64
+ * handle.
  *
  * Units: gravity m in g/cm^3 and d in mGal (gamma = 6.67430e-3 mGal per
  * g/cm^3 per metre); magnetic m = susceptibility (SI) and d = total-field
@@ -66,7 +67,16 @@ typedef enum {
 } gm_status;
 
 typedef enum { GM_GRAVITY = 0, GM_MAGNETIC = 1 } gm_kind;
-typedef enum { GM_F32 = 0, GM_F64 = 1 } gm_precision;
+/* Apply precision.  GM_F32: FP32 vectors and arithmetic.  GM_F64: FP64
+ * vectors and arithmetic.  GM_DF64: FP64 vectors, arithmetic on pairs of
+ * FP32 values (h + l, a 48-bit significand, FP32's exponent range: values
+ * between about 1e-30 and 1e38 in magnitude keep full accuracy), for GPUs
+ * whose FP32 rate far exceeds their FP64 rate; its products agree with the
+ * FP64 ones to about 1e-14 relative.  GM_DF64 runs only on the
+ * register-codelet FFT lengths: it needs s + n - 1 <= 1024 in x and <= 768
+ * in y (the plan always takes the smallest such length); larger grids
+ * return GM_EINVAL at setup. */
+typedef enum { GM_F32 = 0, GM_F64 = 1, GM_DF64 = 2 } gm_precision;
 
 /* Full parameter record for grav_mag_setup_ex.  Sec. 2.1.2 and the parameter
  * table of App. A: stations, layers, cell sizes, left/right padding in x and y,
@@ -145,7 +155,8 @@ typedef struct {
 GM_API gm_status gm_get_info(gm_handle h, gm_info *out);
 
 /* Copies the spectra to host memory: out holds spec_nx * nz * fft_ny complex
- * values (interleaved re, im) in the handle's precision, ordered [kx][r][ky],
+ * values (interleaved re, im) in the handle's vector type (float for GM_F32,
+ * double for GM_F64; GM_DF64 spectra are returned as doubles h + l), ordered [kx][r][ky],
  * i.e. the 2-D FFT of layer r's circulant generator at frequency (kx, ky).
  * bytes must be at least that size (2 * element size * spec_nx * nz * fft_ny).
  * A handle that stores real even spectra (gm_info.spectrum_real) expands them

@@ -38,7 +38,7 @@ namespace {
     } while (0)
 
 template <typename R>
-cudaError_t forward_fast_t(gm_plan *p, const R *m, R *d, cudaStream_t s, int *nl) {
+cudaError_t forward_fast_t(gm_plan *p, const io_t<R> *m, io_t<R> *d, cudaStream_t s, int *nl) {
     using C = cpx_t<R>;
     const Geo &g = p->geo;
     C *A = static_cast<C *>(p->work_big);
@@ -63,7 +63,7 @@ cudaError_t forward_fast_t(gm_plan *p, const R *m, R *d, cudaStream_t s, int *nl
 }
 
 template <typename R>
-cudaError_t transpose_fast_t(gm_plan *p, const R *d, R *m, cudaStream_t s, int *nl) {
+cudaError_t transpose_fast_t(gm_plan *p, const io_t<R> *d, io_t<R> *m, cudaStream_t s, int *nl) {
     using C = cpx_t<R>;
     const Geo &g = p->geo;
     C *D1 = static_cast<C *>(p->work_small);
@@ -119,7 +119,9 @@ void choose_groups(const gm_plan *p, bool tr, int *groups, int *lpg) {
 bool fast_path_supported(int NPx, int NPy) { return x_ops_f32(NPx) != nullptr && y_ops<float>(NPy) != nullptr; }
 
 int fast_column_groups(const gm_plan *p) {
-    const int cols = p->precision == GM_F64 ? y_ops<double>(p->geo.NPy)->cols : y_ops<float>(p->geo.NPy)->cols;
+    const int cols = p->precision == GM_F64    ? y_ops<double>(p->geo.NPy)->cols
+                     : p->precision == GM_DF64 ? y_ops<dfr>(p->geo.NPy)->cols
+                                               : y_ops<float>(p->geo.NPy)->cols;
     return (p->geo.Kx + cols - 1) / cols;
 }
 
@@ -127,6 +129,9 @@ void fast_plan_groups(gm_plan *p) {
     if (p->precision == GM_F64) {
         choose_groups<double>(p, false, &p->fast_groups_fwd, &p->fast_lpg_fwd);
         choose_groups<double>(p, true, &p->fast_groups_tr, &p->fast_lpg_tr);
+    } else if (p->precision == GM_DF64) {
+        choose_groups<dfr>(p, false, &p->fast_groups_fwd, &p->fast_lpg_fwd);
+        choose_groups<dfr>(p, true, &p->fast_groups_tr, &p->fast_lpg_tr);
     } else {
         choose_groups<float>(p, false, &p->fast_groups_fwd, &p->fast_lpg_fwd);
         choose_groups<float>(p, true, &p->fast_groups_tr, &p->fast_lpg_tr);
@@ -136,12 +141,16 @@ void fast_plan_groups(gm_plan *p) {
 cudaError_t launch_forward_fast(gm_plan *p, const void *m, void *d, cudaStream_t s, int *nl) {
     if (p->precision == GM_F64)
         return forward_fast_t<double>(p, static_cast<const double *>(m), static_cast<double *>(d), s, nl);
+    if (p->precision == GM_DF64)
+        return forward_fast_t<dfr>(p, static_cast<const double *>(m), static_cast<double *>(d), s, nl);
     return forward_fast_t<float>(p, static_cast<const float *>(m), static_cast<float *>(d), s, nl);
 }
 
 cudaError_t launch_transpose_fast(gm_plan *p, const void *d, void *m, cudaStream_t s, int *nl) {
     if (p->precision == GM_F64)
         return transpose_fast_t<double>(p, static_cast<const double *>(d), static_cast<double *>(m), s, nl);
+    if (p->precision == GM_DF64)
+        return transpose_fast_t<dfr>(p, static_cast<const double *>(d), static_cast<double *>(m), s, nl);
     return transpose_fast_t<float>(p, static_cast<const float *>(d), static_cast<float *>(m), s, nl);
 }
 

@@ -91,9 +91,10 @@ bool make_radices(int N, FftDesc &d) {
     return n == 1;
 }
 
-cudaError_t make_twiddles(int N, bool f64, void **dev_out) {
+cudaError_t make_twiddles(int N, int precision, void **dev_out) {
     *dev_out = nullptr;
-    size_t elt = f64 ? sizeof(double2) : sizeof(float2);
+    const bool f64 = precision == GM_F64, df = precision == GM_DF64;
+    size_t elt = (f64 || df) ? sizeof(double2) : sizeof(float2);
     std::string host(elt * (size_t)N, '\0');
     for (int e = 0; e < N; ++e) {
         // exp(-2 pi i e / N) in long double, rounded once
@@ -102,6 +103,10 @@ cudaError_t make_twiddles(int N, bool f64, void **dev_out) {
         if (f64) {
             double2 v = make_double2((double)c, (double)s);
             std::memcpy(&host[elt * e], &v, elt);
+        } else if (df) {  // each part rounded to the nearest FP32 pair h + l; order {re.h, im.h, re.l, im.l}
+            const float ch = (float)c, sh = (float)s;
+            const float v[4] = {ch, sh, (float)(c - (long double)ch), (float)(s - (long double)sh)};
+            std::memcpy(&host[elt * e], v, elt);
         } else {
             float2 v = make_float2((float)c, (float)s);
             std::memcpy(&host[elt * e], &v, elt);
@@ -175,7 +180,8 @@ gm_status gm_validate_params(const gm_params *p) {
     if (!(p->dx > 0) || !(p->dy > 0) || !std::isfinite(p->dx) || !std::isfinite(p->dy))
         return fail(GM_EINVAL, "dx, dy must be finite and > 0");
     if (p->kind != GM_GRAVITY && p->kind != GM_MAGNETIC) return fail(GM_EINVAL, "kind must be GM_GRAVITY or GM_MAGNETIC");
-    if (p->precision != GM_F32 && p->precision != GM_F64) return fail(GM_EINVAL, "precision must be GM_F32 or GM_F64");
+    if (p->precision != GM_F32 && p->precision != GM_F64 && p->precision != GM_DF64)
+        return fail(GM_EINVAL, "precision must be GM_F32, GM_F64 or GM_DF64");
     if (p->zplanes) {
         if (!(p->zplanes[0] >= 0) || !std::isfinite(p->zplanes[0])) return fail(GM_EINVAL, "zplanes[0] must be >= 0");
         for (int k = 0; k < p->nz; ++k)
@@ -227,13 +233,15 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
     p->Nx = g.sx + g.nx - 1;
     p->Ny = g.sy + g.ny - 1;
     // FFT lengths: the smallest lengths >= Nx, Ny that the register-codelet kernels are built for
-    // when both are within 25% of the smallest even 7-smooth lengths; otherwise those 7-smooth
-    // lengths (generic kernels).  Any length >= N gives the same products (Sec. 3).
+    // when both are within 25% of the smallest even 7-smooth lengths (always, for GM_DF64, which
+    // has no other kernels); otherwise those 7-smooth lengths (generic kernels).  Any length >= N
+    // gives the same products (Sec. 3).
     {
         const int sx7 = gm_fft_length(p->Nx), sy7 = gm_fft_length(p->Ny);
         const int lx = fast_disabled() ? 0 : gm::fast_ladder_length(p->Nx, false);
         const int ly = fast_disabled() ? 0 : gm::fast_ladder_length(p->Ny, true);
-        const bool ladder = lx && ly && 4 * lx <= 5 * sx7 && 4 * ly <= 5 * sy7;
+        const bool ladder =
+            lx && ly && (prm->precision == GM_DF64 || (4 * lx <= 5 * sx7 && 4 * ly <= 5 * sy7));
         g.NPx = ladder ? lx : sx7;
         g.NPy = ladder ? ly : sy7;
     }
@@ -262,14 +270,19 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
         return nullptr;
     }
     // Memory guard (the paper's memory-safety test, Sec. 6): resident + set-up peak.
-    const size_t cel = prm->precision == GM_F64 ? sizeof(double2) : sizeof(float2);
-    const size_t rel = prm->precision == GM_F64 ? sizeof(double) : sizeof(float);
+    const size_t cel = prm->precision == GM_F32 ? sizeof(float2) : sizeof(double2);
+    const size_t rel = prm->precision == GM_F32 ? sizeof(float) : sizeof(double);
     const size_t nspec = (size_t)g.Kx * g.nz * g.NPy;
     p->spec_bytes = cel * nspec;
     const size_t big = cel * (size_t)g.Kx * g.nz * g.nyp;
     const size_t small = cel * (size_t)g.Kx * g.sy;
     const size_t n_model = (size_t)g.nx * g.ny * g.nz, n_data = (size_t)g.sx * g.sy;
     p->fast = !fast_disabled() && gm::fast_path_supported(g.NPx, g.NPy);
+    if (prm->precision == GM_DF64 && !p->fast) {
+        free_plan(p);
+        fail(GM_EINVAL, "GM_DF64 needs FFT lengths on the register-codelet ladder (here %d x %d)", g.NPx, g.NPy);
+        return nullptr;
+    }
     // gravity with the same padding on both sides: real even spectra, a quarter of the bytes
     // (register-codelet path; GM_COMPLEX_SPECTRA=1 keeps the complex form)
     {
@@ -301,7 +314,6 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
         fail(GM_ENOMEM, "plan needs %zu bytes, %zu free%s", need, freeb, g_mem_limit ? " (or above the set limit)" : "");
         return nullptr;
     }
-    const bool f64 = prm->precision == GM_F64;
 #define SETUP_TRY(x, what)                 \
     do {                                   \
         cudaError_t e_ = (x);              \
@@ -311,8 +323,8 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
             return nullptr;                \
         }                                  \
     } while (0)
-    SETUP_TRY(gm::make_twiddles(g.NPx, f64, &p->tw_x), "twiddles x");
-    SETUP_TRY(gm::make_twiddles(g.NPy, f64, &p->tw_y), "twiddles y");
+    SETUP_TRY(gm::make_twiddles(g.NPx, prm->precision, &p->tw_x), "twiddles x");
+    SETUP_TRY(gm::make_twiddles(g.NPy, prm->precision, &p->tw_y), "twiddles y");
     p->fx.tw = p->tw_x;
     p->fy.tw = p->tw_y;
     SETUP_TRY(cudaMalloc(&p->spec, p->spec_bytes), "spectra");
@@ -364,7 +376,7 @@ static bool overlaps(const void *a, size_t na, const void *b, size_t nb) {
 static gm_status check_apply(gm_handle h, const void *in, size_t nin, const void *out, size_t nout) {
     if (!h) return fail(GM_EINVAL, "handle is NULL");
     if (!in || !out) return fail(GM_EINVAL, "NULL buffer");
-    const size_t rel = h->precision == GM_F64 ? sizeof(double) : sizeof(float);
+    const size_t rel = h->precision == GM_F32 ? sizeof(float) : sizeof(double);
     if (overlaps(in, nin * rel, out, nout * rel)) return fail(GM_EINVAL, "input and output overlap");
     return GM_OK;
 }
@@ -409,7 +421,7 @@ static gm_status host_apply(gm_handle h, const void *in_host, void *out_host, vo
     if (!h) return fail(GM_EINVAL, "handle is NULL");
     if (!in_host || !out_host) return fail(GM_EINVAL, "NULL buffer");
     DeviceGuard dg(h->device);
-    const size_t rel = h->precision == GM_F64 ? sizeof(double) : sizeof(float);
+    const size_t rel = h->precision == GM_F32 ? sizeof(float) : sizeof(double);
     const size_t n = (size_t)h->geo.nx * h->geo.ny * h->geo.nz, m = (size_t)h->geo.sx * h->geo.sy;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // Page-locked buffers are read and written in place by the kernels (over the host link), with
@@ -475,11 +487,11 @@ gm_status gm_get_info(gm_handle h, gm_info *out) {
 gm_status gm_copy_spectrum(gm_handle h, void *host_out, size_t bytes) {
     if (!h || !host_out) return fail(GM_EINVAL, "NULL argument");
     const gm::Geo &g = h->geo;
-    const size_t el = h->precision == GM_F64 ? sizeof(double) : sizeof(float);
+    const size_t el = h->precision == GM_F32 ? sizeof(float) : sizeof(double);
     const size_t need = 2 * el * (size_t)g.Kx * g.nz * g.NPy;
     if (bytes < need) return fail(GM_EINVAL, "buffer smaller than spec_nx * nz * fft_ny complex values");
     DeviceGuard dg(h->device);
-    if (!h->spec_real) {
+    if (!h->spec_real && h->precision != GM_DF64) {
         cudaError_t e = cudaMemcpy(host_out, h->spec, h->spec_bytes, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "copy spectrum");
         return ok();
@@ -487,6 +499,23 @@ gm_status gm_copy_spectrum(gm_handle h, void *host_out, size_t bytes) {
     std::vector<unsigned char> tmp(h->spec_bytes);
     cudaError_t e = cudaMemcpy(tmp.data(), h->spec, h->spec_bytes, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "copy spectrum");
+    if (h->precision == GM_DF64) {  // pairs of floats h + l -> doubles
+        const size_t nv = h->spec_bytes / (2 * sizeof(float));
+        std::vector<double> v(nv);
+        const float *f = reinterpret_cast<const float *>(tmp.data());
+        if (h->spec_real)  // reals {h, l}
+            for (size_t i = 0; i < nv; ++i) v[i] = (double)f[2 * i] + (double)f[2 * i + 1];
+        else  // complex {re.h, im.h, re.l, im.l}
+            for (size_t i = 0; i < nv; i += 2) {
+                v[i] = (double)f[2 * i] + (double)f[2 * i + 2];
+                v[i + 1] = (double)f[2 * i + 1] + (double)f[2 * i + 3];
+            }
+        if (h->spec_real)
+            expand_real_spectrum<double>(h, v.data(), static_cast<double *>(host_out));
+        else
+            std::memcpy(host_out, v.data(), sizeof(double) * nv);
+        return ok();
+    }
     if (h->precision == GM_F64)
         expand_real_spectrum<double>(h, reinterpret_cast<const double *>(tmp.data()), static_cast<double *>(host_out));
     else

@@ -117,9 +117,13 @@ __global__ void k_beta(const double *part, double *sc, double *resid, int k) {
 }
 
 // Convergence threshold on ||s||^2 / ||s_0||^2 for vectors of type R.
-template <typename R> constexpr double cgls_tol2() {
-    return (64.0 * (sizeof(R) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07)) *
-           (64.0 * (sizeof(R) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07));
+// squared freeze threshold: 64 units of the apply arithmetic's precision (double-float pairs
+// carry a 48-bit significand, 2^-47 apart)
+inline double cgls_tol2(int precision) {
+    const double eps = precision == GM_F64    ? 2.220446049250313e-16
+                       : precision == GM_DF64 ? 7.105427357601002e-15
+                                              : 1.1920928955078125e-07;
+    return (64.0 * eps) * (64.0 * eps);
 }
 
 // r = d - r (r holds G x0 on entry)
@@ -213,7 +217,7 @@ static cudaError_t cgls_t(gm_plan *p, const R *d, const R *x0, R *x, double alph
     }
     launch_pdl(k_s_update<R>, dim3(vb), dim3(vt), 0, st, s, x, pv, n, (R)(alpha * alpha), 1);
     launch_pdl(k_sumsq2<R>, dim3(vb), dim3(vt), 0, st, s, n, r, m, part);
-    launch_pdl(k_init_scalars, dim3(1), dim3(1024), 0, st, part, sc, resid, alpha * alpha, cgls_tol2<R>());
+    launch_pdl(k_init_scalars, dim3(1), dim3(1024), 0, st, part, sc, resid, alpha * alpha, cgls_tol2(p->precision));
     launches += 4;
     for (k = 1; k <= iters; ++k) {
         int l = 0;
@@ -277,7 +281,7 @@ static cudaError_t noalloc_scratch(void **out) {
 
 size_t noalloc_cgls_need(const gm_plan *p, int iters) {
     const size_t n = (size_t)p->geo.nx * p->geo.ny * p->geo.nz, m = (size_t)p->geo.sx * p->geo.sy;
-    const size_t el = p->precision == GM_F64 ? sizeof(double) : sizeof(float);
+    const size_t el = p->precision == GM_F32 ? sizeof(float) : sizeof(double);
     return ((el * (2 * n + 2 * m) + 255) / 256) * 256 + sizeof(double) * (2 * kRedBlocks + S_COUNT + (size_t)iters + 1);
 }
 
@@ -320,7 +324,7 @@ static cudaError_t cgls_noalloc_t(gm_plan *p, const R *d, const R *x0, R *x, dou
     }
     launch_pdl(k_s_update<R>, dim3(vb), dim3(vt), 0, st, s, x, pv, n, (R)(alpha * alpha), 1);
     launch_pdl(k_sumsq2<R>, dim3(vb), dim3(vt), 0, st, s, n, r, m, part);
-    launch_pdl(k_init_scalars, dim3(1), dim3(1024), 0, st, part, sc, resid, alpha * alpha, cgls_tol2<R>());
+    launch_pdl(k_init_scalars, dim3(1), dim3(1024), 0, st, part, sc, resid, alpha * alpha, cgls_tol2(p->precision));
     launches += 4;
     for (k = 1; k <= iters; ++k) {
         int l = 0;
@@ -351,7 +355,7 @@ out:
 
 cudaError_t run_cgls_noalloc(gm_plan *p, const void *d, const void *x0, void *x, double alpha, int iters,
                              double *resid_host, cudaStream_t s, int *nl) {
-    if (p->precision == GM_F64)
+    if (p->precision != GM_F32)  // FP64 vectors (GM_F64, GM_DF64)
         return cgls_noalloc_t<double>(p, static_cast<const double *>(d), static_cast<const double *>(x0),
                                       static_cast<double *>(x), alpha, iters, resid_host, s, nl);
     return cgls_noalloc_t<float>(p, static_cast<const float *>(d), static_cast<const float *>(x0),
@@ -360,7 +364,7 @@ cudaError_t run_cgls_noalloc(gm_plan *p, const void *d, const void *x0, void *x,
 
 cudaError_t run_cgls(gm_plan *p, const void *d, const void *x0, void *x, double alpha, int iters, double *resid_host,
                      cudaStream_t s, int *nl) {
-    if (p->precision == GM_F64)
+    if (p->precision != GM_F32)  // FP64 vectors (GM_F64, GM_DF64)
         return cgls_t<double>(p, static_cast<const double *>(d), static_cast<const double *>(x0),
                               static_cast<double *>(x), alpha, iters, resid_host, s, nl);
     return cgls_t<float>(p, static_cast<const float *>(d), static_cast<const float *>(x0), static_cast<float *>(x),

@@ -331,7 +331,7 @@ def codelet(n, inverse, nin=None):
     body += [f"    v[{k}] = {out[k] if out[k] else 'C{}'};" for k in range(n)]
     name = ("idft" if inverse else "dft") + str(n) + ("" if nin == n else f"_in{nin}")
     return (f"template <typename C>\n__device__ __forceinline__ void {name}(C (&v)[{n}]) {{\n"
-            f"    using R = decltype(v[0].x);\n" + "\n".join(body) + "\n}\n")
+            f"    using R = typename real_of<C>::type;\n" + "\n".join(body) + "\n}\n")
 
 
 # input-pruned variants: sizes used as the first pass of zero-padded transforms, with the
@@ -377,7 +377,7 @@ def main():
     parts = ["// gm_fft_codelets.cuh -- GENERATED by gen_fft_codelets.py; do not edit by hand.",
              "// Straight-line in-register DFTs, natural order: dftN (forward, exp(-2 pi i nk/N)) and",
              "// idftN (inverse, exp(+2 pi i nk/N), unnormalised), for C = float2 or double2.",
-             "#pragma once", "", "#include <cuda_runtime.h>", "", "namespace gm {", "namespace cl {", PRELUDE]
+             "#pragma once", "", "#include <cuda_runtime.h>", "", "#include \"gm_common.cuh\"", "", "namespace gm {", "namespace cl {", PRELUDE]
     for n in SIZES:
         parts.append(codelet(n, False))
         parts.append(codelet(n, True))

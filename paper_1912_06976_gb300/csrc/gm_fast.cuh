@@ -78,6 +78,41 @@ __device__ __forceinline__ double2 ld_hint(const double2 *p, uint64_t pol) {
     asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
     return v;
 }
+__device__ __forceinline__ dfr ld_hint(const dfr *p, uint64_t pol) {
+    dfr v;
+    asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.h), "=f"(v.l) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ dfc ld_hint(const dfc *p, uint64_t pol) {
+    dfc v;
+    asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.h.x), "=f"(v.h.y), "=f"(v.l.x), "=f"(v.l.y)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_hint(dfc *p, dfc v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.h.x), "f"(v.h.y),
+                 "f"(v.l.x), "f"(v.l.y), "l"(pol)
+                 : "memory");
+}
+// read-only (non-coherent) load of data no kernel writes while this one runs
+__device__ __forceinline__ float2 ld_nc(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ double2 ld_nc(const double2 *p) { return __ldg(p); }
+__device__ __forceinline__ dfc ld_nc(const dfc *p) {
+    dfc v;
+    asm("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.h.x), "=f"(v.h.y), "=f"(v.l.x), "=f"(v.l.y) : "l"(p));
+    return v;
+}
+// load cached in L2 only (values other blocks of the same kernel wrote)
+__device__ __forceinline__ float2 ld_cg(const float2 *p) { return __ldcg(p); }
+__device__ __forceinline__ double2 ld_cg(const double2 *p) { return __ldcg(p); }
+__device__ __forceinline__ dfc ld_cg(const dfc *p) {
+    dfc v;
+    asm volatile("ld.global.cg.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.h.x), "=f"(v.h.y), "=f"(v.l.x), "=f"(v.l.y)
+                 : "l"(p));
+    return v;
+}
 __device__ __forceinline__ void st_hint(float2 *p, float2 v, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol)
                  : "memory");
@@ -151,7 +186,7 @@ __device__ __forceinline__ void pass2_twiddle_table(C (&v)[R2], const C *__restr
 #pragma unroll
     for (int rr = 1; rr < R2; ++rr) {
         C w = tw[rr * j];
-        if (INV) w.y = -w.y;
+        if (INV) w = c_conj(w);
         v[rr] = c_mul(v[rr], w);
     }
 }
@@ -164,7 +199,7 @@ __device__ __forceinline__ void load_table(C *dst, const C *__restrict__ src) {
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         const int i = threadIdx.x + b * THREADS;
-        if (i < N) tmp[b] = __ldg(src + i);
+        if (i < N) tmp[b] = ld_nc(src + i);
     }
 #pragma unroll
     for (int b = 0; b < B; ++b) {
@@ -200,8 +235,10 @@ __global__ void __launch_bounds__(THREADS) k_rows_r2c(const Rin *__restrict__ in
         for (int rr = 0; rr < R1; ++rr) {
             const int n = j + R2 * rr;
             const bool ok = n < row_len;
-            v[rr].x = (ok && va) ? (decltype(v[0].x))ld_hint(ra + n, pol_in) : 0;
-            v[rr].y = (ok && vb) ? (decltype(v[0].x))ld_hint(ra + row_len + n, pol_in) : 0;
+            using Re = typename real_of<C>::type;
+            const Re re = (ok && va) ? (Re)ld_hint(ra + n, pol_in) : Re(0);
+            const Re im = (ok && vb) ? (Re)ld_hint(ra + row_len + n, pol_in) : Re(0);
+            v[rr] = c_make<C>(re, im);
         }
         pass1_store<R1, false>(v, ex + p * EX, j);
     }
@@ -230,11 +267,8 @@ __global__ void __launch_bounds__(THREADS) k_rows_r2c(const Rin *__restrict__ in
         if (qa >= rows) continue;
         const C a = ex[p * EX + k];
         const C b = c_conj(ex[p * EX + (k == 0 ? 0 : N - k)]);
-        C x1, x2;
-        x1.x = (a.x + b.x) * 0.5f;
-        x1.y = (a.y + b.y) * 0.5f;
-        x2.x = (a.y - b.y) * 0.5f;
-        x2.y = (b.x - a.x) * 0.5f;
+        const C x1 = c_half(c_add(a, b));               // (Z[k] + conj Z[-k]) / 2
+        const C x2 = c_half(c_mul_mi(c_sub(a, b)));     // (Z[k] - conj Z[-k]) / 2i
         C *o = out + ((size_t)k * nlayers + layer) * out_rows + qa;
         st_hint(o, x1, pol_out);
         if (qa + 1 < rows) st_hint(o + 1, x2, pol_out);
@@ -303,15 +337,16 @@ __global__ void __launch_bounds__(THREADS) k_rows_c2r(const C *__restrict__ in, 
             const int n = j + R2 * rr;
             const int kk = (n <= H) ? n : N - n;
             C a = x1r[kk], b = x2r[kk];
-            if (n > H) { a.y = -a.y; b.y = -b.y; }
-            v[rr] = c_make<C>(a.x - b.y, a.y + b.x);  // X1 + i X2
+            if (n > H) { a = c_conj(a); b = c_conj(b); }
+            v[rr] = c_add(a, c_mul_i(b));  // X1 + i X2
         }
         __syncwarp(R2 >= 32 ? 0xffffffffu : ((1u << R2) - 1u));  // the pair's rows are in registers
         pass1_store<R1, true>(v, ex, j);
     }
     __syncwarp();
     pdl_trigger();
-    const auto sc = (decltype(ex[0].x))scale;
+    using Re = typename real_of<C>::type;
+    const Re sc = (Re)scale;
     if (lane < R1) {
         const int j = lane;
         C v[R2];
@@ -324,8 +359,8 @@ __global__ void __launch_bounds__(THREADS) k_rows_c2r(const C *__restrict__ in, 
         for (int s = 0; s < R2; ++s) {
             const int i = j + R1 * s;
             if (i < row_len_out) {
-                if (qa < rows) oa[i] = (Rout)(v[s].x * sc);
-                if (qa + 1 < rows) oa[row_len_out + i] = (Rout)(v[s].y * sc);
+                if (qa < rows) oa[i] = (Rout)(c_re(v[s]) * sc);
+                if (qa + 1 < rows) oa[row_len_out + i] = (Rout)(c_im(v[s]) * sc);
             }
         }
     }
@@ -350,7 +385,7 @@ __device__ __forceinline__ void cols_sum_inverse(const C *__restrict__ part, int
                 const C *pg = part + ((size_t)g * Kx + kx) * N + j;
                 C tmp[IR1];
 #pragma unroll
-                for (int rr = 0; rr < IR1; ++rr) tmp[rr] = __ldcg(pg + IR2 * rr);  // written by other CTAs
+                for (int rr = 0; rr < IR1; ++rr) tmp[rr] = ld_cg(pg + IR2 * rr);  // written by other CTAs
 #pragma unroll
                 for (int rr = 0; rr < IR1; ++rr) v[rr] = c_add(v[rr], tmp[rr]);
             }
@@ -449,8 +484,7 @@ __global__ void __launch_bounds__(THREADS)
 #pragma unroll
                         for (int s = 0; s < R2; ++s) {
                             const Rr e = ld_hint(Er + even_index<R1, R2>(oj, s), pol_s);
-                            acc[s].x += v[s].x * e;
-                            acc[s].y += v[s].y * e;
+                            acc[s] = c_fma(v[s], e, acc[s]);
                         }
                     } else {
                         const C *Sr = S + ((size_t)okx * nz + rl) * N + oj;
@@ -564,7 +598,7 @@ __global__ void __launch_bounds__(THREADS)
 #pragma unroll
                         for (int s = 0; s < R2; ++s) {
                             const Rr e = ld_hint(Er + even_index<R1, R2>(oj, s), pol_s);
-                            v[s] = c_make<C>(dh[s].x * e, dh[s].y * e);
+                            v[s] = c_scale(dh[s], e);
                         }
                     } else {
                         const C *Sr = S + ((size_t)okx * nz + rl) * N + oj;

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "gm_fast.cuh"
 #include "gm_fast_ops.h"
@@ -26,11 +27,11 @@ template <int R1> constexpr int cols_per_cta() { return 256 / R1 > 0 ? 256 / R1 
 
 // ---- x-direction (rows): r2c with radices (X1, X2), c2r with (X2, X1)
 template <typename R, int X1, int X2, int PAIRS, int THREADS>
-cudaError_t rows_r2c_p(const R *in, int rows, int row_len, int nlayers, cpx_t<R> *out, int out_rows,
+cudaError_t rows_r2c_p(const io_t<R> *in, int rows, int row_len, int nlayers, cpx_t<R> *out, int out_rows,
                        const void *tw, cudaStream_t s) {
     using C = cpx_t<R>;
     const size_t sm = sizeof(C) * (PAIRS * fast::Ex<X1, X2>::value);
-    auto k = fast::k_rows_r2c<C, R, X1, X2, PAIRS, THREADS>;
+    auto k = fast::k_rows_r2c<C, io_t<R>, X1, X2, PAIRS, THREADS>;
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
     dim3 grd((rows + 2 * PAIRS - 1) / (2 * PAIRS), nlayers);
@@ -40,16 +41,18 @@ cudaError_t rows_r2c_p(const R *in, int rows, int row_len, int nlayers, cpx_t<R>
 }
 
 template <typename R, int X1, int X2>
-cudaError_t rows_r2c(const R *in, int rows, int row_len, int nlayers, cpx_t<R> *out, int out_rows,
+cudaError_t rows_r2c(const io_t<R> *in, int rows, int row_len, int nlayers, cpx_t<R> *out, int out_rows,
                      const void *tw, cudaStream_t s) {
     static_assert(X1 <= 32 && X2 <= 32, "one-warp CTAs hold one item of each pass per thread");
-    if (few_rows(rows, nlayers)) return rows_r2c_p<R, X1, X2, 1, 32>(in, rows, row_len, nlayers, out, out_rows, tw, s);
+    // (double-float builds only the many-rows form: its straight-line code is large to compile)
+    if constexpr (!std::is_same<R, dfr>::value)
+        if (few_rows(rows, nlayers)) return rows_r2c_p<R, X1, X2, 1, 32>(in, rows, row_len, nlayers, out, out_rows, tw, s);
     return rows_r2c_p<R, X1, X2, kPairs, 256>(in, rows, row_len, nlayers, out, out_rows, tw, s);
 }
 
 template <typename R, int X1, int X2, int PAIRS, int THREADS>
 cudaError_t rows_c2r_p(const cpx_t<R> *in, long long ld_k, long long ld_layer, long long ld_row, int rows,
-                       int nlayers, R *out, int row_len_out, double scale, const void *tw, bool discard,
+                       int nlayers, io_t<R> *out, int row_len_out, double scale, const void *tw, bool discard,
                        cudaStream_t s) {
     using C = cpx_t<R>;
     constexpr int N = X1 * X2, Kx = N / 2 + 1;
@@ -61,7 +64,7 @@ cudaError_t rows_c2r_p(const cpx_t<R> *in, long long ld_k, long long ld_layer, l
                          : 0;
     // inverse radices (X2, X1): pass-2 items j < X2 write X2-wide coalesced rows
     const size_t sm = sizeof(C) * PAIRS * fast::C2rRegion<X2, X1>::value;
-    auto k = fast::k_rows_c2r<C, R, X2, X1, PAIRS, THREADS>;
+    auto k = fast::k_rows_c2r<C, io_t<R>, X2, X1, PAIRS, THREADS>;
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
     dim3 grd((rows + 2 * PAIRS - 1) / (2 * PAIRS), nlayers);
@@ -73,11 +76,12 @@ cudaError_t rows_c2r_p(const cpx_t<R> *in, long long ld_k, long long ld_layer, l
 
 template <typename R, int X1, int X2>
 cudaError_t rows_c2r(const cpx_t<R> *in, long long ld_k, long long ld_layer, long long ld_row, int rows,
-                     int nlayers, R *out, int row_len_out, double scale, const void *tw, bool discard,
+                     int nlayers, io_t<R> *out, int row_len_out, double scale, const void *tw, bool discard,
                      cudaStream_t s) {
-    if (few_rows(rows, nlayers))
-        return rows_c2r_p<R, X1, X2, 1, 32>(in, ld_k, ld_layer, ld_row, rows, nlayers, out, row_len_out, scale, tw,
-                                            discard, s);
+    if constexpr (!std::is_same<R, dfr>::value)
+        if (few_rows(rows, nlayers))
+            return rows_c2r_p<R, X1, X2, 1, 32>(in, ld_k, ld_layer, ld_row, rows, nlayers, out, row_len_out, scale,
+                                                tw, discard, s);
     return rows_c2r_p<R, X1, X2, kPairs, 256>(in, ld_k, ld_layer, ld_row, rows, nlayers, out, row_len_out, scale,
                                               tw, discard, s);
 }

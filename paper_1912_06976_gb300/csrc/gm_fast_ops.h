@@ -27,10 +27,10 @@ struct gm_plan;
 namespace gm {
 
 template <typename R> struct XOps {
-    cudaError_t (*r2c)(const R *in, int rows, int row_len, int nlayers, cpx_t<R> *out, int out_rows, const void *tw,
+    cudaError_t (*r2c)(const io_t<R> *in, int rows, int row_len, int nlayers, cpx_t<R> *out, int out_rows, const void *tw,
                        cudaStream_t s);
     cudaError_t (*c2r)(const cpx_t<R> *in, long long ld_k, long long ld_layer, long long ld_row, int rows,
-                       int nlayers, R *out, int row_len_out, double scale, const void *tw, bool discard,
+                       int nlayers, io_t<R> *out, int row_len_out, double scale, const void *tw, bool discard,
                        cudaStream_t s);
 };
 
@@ -50,10 +50,13 @@ const YOps<float> *y_ops_f32(int N);
 const YOps<double> *y_ops_f64(int N);
 const YOps<float> *y_ops_f32_large(int N);
 const YOps<double> *y_ops_f64_large(int N);
+const XOps<dfr> *x_ops_df(int N);
+const YOps<dfr> *y_ops_df(int N);
 
 template <typename R> const XOps<R> *x_ops(int N);
 template <> inline const XOps<float> *x_ops<float>(int N) { return x_ops_f32(N); }
 template <> inline const XOps<double> *x_ops<double>(int N) { return x_ops_f64(N); }
+template <> inline const XOps<dfr> *x_ops<dfr>(int N) { return x_ops_df(N); }
 template <typename R> const YOps<R> *y_ops(int N);
 template <> inline const YOps<float> *y_ops<float>(int N) {
     const YOps<float> *o = y_ops_f32(N);
@@ -63,6 +66,8 @@ template <> inline const YOps<double> *y_ops<double>(int N) {
     const YOps<double> *o = y_ops_f64(N);
     return o ? o : y_ops_f64_large(N);
 }
+
+template <> inline const YOps<dfr> *y_ops<dfr>(int N) { return y_ops_df(N); }
 
 // smallest ladder length >= n in the row (y = false) or column (y = true) direction, or 0
 int fast_ladder_length(int n, bool y);

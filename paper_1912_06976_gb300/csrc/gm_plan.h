@@ -86,7 +86,7 @@ bool make_radices(int N, FftDesc &d);
 
 // Twiddle table exp(-2 pi i e / N), e < N, computed on the host in long double
 // and rounded to the element type; allocated on the device.
-cudaError_t make_twiddles(int N, bool f64, void **dev_out);
+cudaError_t make_twiddles(int N, int precision, void **dev_out);  // table exp(-2 pi i e / N) in a gm_precision
 
 // Set-up: FP64 entries -> generators -> FP64 2-D FFT -> spectra in the plan's precision.
 cudaError_t build_spectra(gm_plan *p, cudaStream_t s);

@@ -115,6 +115,13 @@ __global__ void k_round_to_f32(const double2 *__restrict__ in, float2 *__restric
         out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
 
+// FP64 spectra -> double-float pairs (GM_DF64): each part rounded to the nearest h + l
+__global__ void k_split_df(const double2 *__restrict__ in, dfc *__restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        out[i] = c_make<dfc>(dfr(in[i].x), dfr(in[i].y));
+    }
+}
+
 #define GM_TRY(x)                              \
     do {                                       \
         cudaError_t e_ = (x);                  \
@@ -181,8 +188,8 @@ cudaError_t build_spectra(gm_plan *p, cudaStream_t s) {
         tw64x = p->tw_x;
         tw64y = p->tw_y;
     } else {
-        GM_TRY(make_twiddles(g.NPx, true, &tw64x));
-        GM_TRY(make_twiddles(g.NPy, true, &tw64y));
+        GM_TRY(make_twiddles(g.NPx, GM_F64, &tw64x));
+        GM_TRY(make_twiddles(g.NPy, GM_F64, &tw64y));
     }
     fx64.tw = tw64x;
     fy64.tw = tw64y;
@@ -223,6 +230,9 @@ cudaError_t build_spectra(gm_plan *p, cudaStream_t s) {
         if (p->precision == GM_F64)
             k_real_even_spectrum<double><<<1024, 256, 0, s>>>(S64, static_cast<double *>(p->spec), g.Kx, g.nz, g.NPx,
                                                               g.NPy, g.pxl, g.pyl, dev);
+        else if (p->precision == GM_DF64)
+            k_real_even_spectrum<dfr><<<1024, 256, 0, s>>>(S64, static_cast<dfr *>(p->spec), g.Kx, g.nz, g.NPx,
+                                                           g.NPy, g.pxl, g.pyl, dev);
         else
             k_real_even_spectrum<float><<<1024, 256, 0, s>>>(S64, static_cast<float *>(p->spec), g.Kx, g.nz, g.NPx,
                                                              g.NPy, g.pxl, g.pyl, dev);
@@ -240,6 +250,9 @@ cudaError_t build_spectra(gm_plan *p, cudaStream_t s) {
         }
     } else if (p->precision == GM_F64) {
         GM_TRY(cudaMemcpyAsync(p->spec, S64, sizeof(double2) * nspec, cudaMemcpyDeviceToDevice, s));
+    } else if (p->precision == GM_DF64) {
+        k_split_df<<<1024, 256, 0, s>>>(S64, static_cast<dfc *>(p->spec), nspec);
+        GM_TRY(cudaGetLastError());
     } else {
         k_round_to_f32<<<1024, 256, 0, s>>>(S64, reinterpret_cast<float2 *>(p->spec), nspec);
         GM_TRY(cudaGetLastError());

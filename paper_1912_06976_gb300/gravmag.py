@@ -24,6 +24,7 @@ GRAVITY = 0
 MAGNETIC = 1
 F32 = 0
 F64 = 1
+DF64 = 2  # FP64 vectors, arithmetic on pairs of FP32 values (see include/gravmag.h)
 
 GM_OK, GM_EINVAL, GM_ENOMEM, GM_ECUDA, GM_ETIMEOUT, GM_EDEVICE, GM_ENODEV = range(7)
 _STATUS_NAMES = ["GM_OK", "GM_EINVAL", "GM_ENOMEM", "GM_ECUDA", "GM_ETIMEOUT", "GM_EDEVICE", "GM_ENODEV"]
@@ -164,8 +165,8 @@ class Operator:
     """The fast operator G of one geometry: ``forward(m) = G m``, ``transpose(d) = G^T d``.
 
     Wraps one C-ABI handle (spectra and workspace live on the GPU that is
-    current at construction).  ``precision`` is F32 or F64; tensors passed in
-    must be CUDA tensors of the matching dtype.
+    current at construction).  ``precision`` is F32, F64 or DF64; tensors passed
+    in must be CUDA tensors of the matching dtype (float32 for F32, float64 otherwise).
     """
 
     def __init__(self, sx, sy, nz, dx, dy, dz=None, *, px=0, py=0, pxr=None, pyr=None, zplanes=None,
@@ -195,7 +196,7 @@ class Operator:
     def dtype(self):
         import torch
 
-        return torch.float64 if self.precision == F64 else torch.float32
+        return torch.float32 if self.precision == F32 else torch.float64
 
     @property
     def model_shape(self):
@@ -266,7 +267,7 @@ class Operator:
     def spectrum(self) -> np.ndarray:
         """The stored spectra as complex numpy array [spec_nx, nz, fft_ny]."""
         inf = self.info
-        dt = np.complex128 if self.precision == F64 else np.complex64
+        dt = np.complex64 if self.precision == F32 else np.complex128
         out = np.empty((inf.spec_nx, inf.nz, inf.fft_ny), dtype=dt)
         _check(load().gm_copy_spectrum(self._h, ctypes.c_void_p(out.ctypes.data), out.nbytes))
         return out
@@ -356,4 +357,4 @@ def rel_err(x, ref) -> float:
 
 
 __all__ = ["Operator", "gravmag_apply", "load", "fft_length", "validate", "make_params", "set_memory_limit",
-           "GravMagError", "GRAVITY", "MAGNETIC", "F32", "F64"]
+           "GravMagError", "GRAVITY", "MAGNETIC", "F32", "F64", "DF64"]

@@ -4,8 +4,8 @@
   L(m) = 1/2 ||G m - d||^2 is checked against central finite differences of L
   evaluated with the FP64 operator on 32 random directions, and the FP32
   dot-product test holds to 1e-6 (128 x 128 x 32 magnetic grid, I = 60, D = 0).
-* CGLS on the device converges to the Tikhonov solution
-  (G^T G + alpha^2 I)^-1 G^T d computed densely from oracle entries, and on the
+* CGLS on the device (FP64 and double-float handles) converges to the Tikhonov
+  solution (G^T G + alpha^2 I)^-1 G^T d computed densely from oracle entries, and on the
   128 x 128 x 32 grid its reported residuals match ||G x_k - d|| recomputed.
 """
 import numpy as np
@@ -92,7 +92,8 @@ def _cpu_tikhonov(G, d, alpha):
 
 
 @pytest.mark.parametrize("kind", [W.GRAVITY, W.MAGNETIC])
-def test_cgls_converges_to_tikhonov_solution(gm, kind):
+@pytest.mark.parametrize("prec", ["F64", "DF64"])
+def test_cgls_converges_to_tikhonov_solution(gm, kind, prec):
     """200 CGLS iterations reach the exact regularised solution.  alpha = 0.3 ||G|| keeps the
     condition number of G^T G + alpha^2 I near 12, so CG's error bound (((sqrt(k)-1)/(sqrt(k)+1))^i)
     is far below rounding after 200 iterations."""
@@ -104,7 +105,7 @@ def test_cgls_converges_to_tikhonov_solution(gm, kind):
     alpha = 0.3 * float(np.linalg.norm(G, 2))
     x_ref = _cpu_tikhonov(G, d.ravel(), alpha)
     op = gm.Operator(4, 3, 2, 20.0, 25.0, 15.0, px=1, py=1, kind=kind, incl_deg=50.0, decl_deg=8.0,
-                     precision=gm.F64)
+                     precision=getattr(gm, prec))
     dt = torch.as_tensor(d, device="cuda")
     x, res = op.cgls(dt, alpha, 200)
     assert rel_err(x.cpu().numpy(), x_ref) < 1e-9

@@ -1,6 +1,7 @@
-"""Every FFT length of the register-codelet ladder, in the row and the column direction, FP32
-and FP64: against the oracle at sampled stations and cells, and against the generic kernels
-(selected with GM_GENERIC_FFT=1) over the whole vector.
+"""Every FFT length of the register-codelet ladder, in the row and the column direction, FP32,
+FP64 and double-float (DF64): against the oracle at sampled stations and cells, and over the
+whole vector against the generic kernels (selected with GM_GENERIC_FFT=1; DF64, which has no
+generic kernels, against the FP64 codelet run).
 
 A geometry with s stations and no padding has N = 2 s - 1; s = L / 2 makes the plan pick the
 ladder length L.  The other direction is kept at 16 stations (length 32), with two layers and a
@@ -17,7 +18,7 @@ pytestmark = pytest.mark.gpu
 X_LADDER = [32, 48, 64, 80, 96, 112, 128, 140, 160, 192, 224, 256, 288, 320, 384, 448, 512, 560, 576, 640, 672,
             768, 896, 1024]
 Y_LADDER = [32, 48, 64, 80, 96, 112, 128, 140, 160, 192, 224, 256, 288, 320, 384, 448, 512, 560, 576, 640, 672, 768]
-TOL = {1: 1e-12, 0: 1e-5}
+TOL = {1: 1e-12, 0: 1e-5, 2: 1e-12}
 
 
 def _case(direction, L, i):
@@ -30,7 +31,7 @@ def _case(direction, L, i):
 CASES = [("x", L, i) for i, L in enumerate(X_LADDER)] + [("y", L, i) for i, L in enumerate(Y_LADDER)]
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("direction,L,i", CASES, ids=[f"{d}{L}" for d, L, _ in CASES])
 def test_ladder_length_vs_oracle_and_generic(gm, monkeypatch, direction, L, i, prec):
     import torch
@@ -40,10 +41,10 @@ def test_ladder_length_vs_oracle_and_generic(gm, monkeypatch, direction, L, i, p
                       w.decl_deg, w.F_nT)
     m = W.random_vector(w.model_shape, 40 + i)
     d = W.random_vector(w.data_shape, 80 + i)
-    dt = torch.float64 if prec == 1 else torch.float32
+    dt = torch.float32 if prec == 0 else torch.float64
 
-    def run():
-        op = gm.Operator.from_workload(w, precision=prec)
+    def run(p=prec):
+        op = gm.Operator.from_workload(w, precision=p)
         info = op.get_info()
         f = op.forward(torch.as_tensor(m, dtype=dt, device="cuda")).double().cpu().numpy()
         t = op.transpose(torch.as_tensor(d, dtype=dt, device="cuda")).double().cpu().numpy()
@@ -57,9 +58,12 @@ def test_ladder_length_vs_oracle_and_generic(gm, monkeypatch, direction, L, i, p
     ce = np.sort(rng.choice(w.nx * w.ny * w.nz, size=48, replace=False))
     assert rel_err(f.ravel()[st], O.forward(geom, m, stations=st)) < TOL[prec]
     assert rel_err(t.ravel()[ce], O.transpose(geom, d, cells=ce)) < TOL[prec]
-    monkeypatch.setenv("GM_GENERIC_FFT", "1")
-    _, fg, tg = run()
-    monkeypatch.delenv("GM_GENERIC_FFT")
-    tol = 1e-13 if prec == 1 else 3e-6
+    if prec == 2:
+        _, fg, tg = run(1)
+    else:
+        monkeypatch.setenv("GM_GENERIC_FFT", "1")
+        _, fg, tg = run()
+        monkeypatch.delenv("GM_GENERIC_FFT")
+    tol = 3e-6 if prec == 0 else 1e-13
     assert rel_err(f, fg) < tol
     assert rel_err(t, tg) < tol

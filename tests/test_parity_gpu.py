@@ -1,7 +1,9 @@
 """GPU products against the CPU oracle (the parity gate).
 
 FP64 applies must match the long-double dense oracle to a relative 2-norm error
-of 1e-12, FP32 applies to 1e-5 (the paper's measure, Sec. 5).  Small cases are
+of 1e-12, FP32 applies to 1e-5 (the paper's measure, Sec. 5).  Double-float
+(DF64: FP64 vectors, arithmetic on pairs of FP32 values) applies are held to
+the FP64 gate.  Small cases are
 compared element by element over the whole vector; the large workloads at
 sampled stations / cells the oracle computes one by one (stored by
 tests/golden/make_golden.py, which calls only the oracle).
@@ -18,7 +20,7 @@ from tests.conftest import rel_err
 
 pytestmark = pytest.mark.gpu
 
-TOL = {1: 1e-12, 0: 1e-5}  # precision -> relative 2-norm tolerance
+TOL = {1: 1e-12, 0: 1e-5, 2: 1e-12}  # precision (F64, F32, DF64) -> relative 2-norm tolerance
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
@@ -31,7 +33,7 @@ def run(gm, w, prec, m, d):
     import torch
 
     op = gm.Operator.from_workload(w, precision=prec)
-    dt = torch.float64 if prec == gm.F64 else torch.float32
+    dt = torch.float32 if prec == gm.F32 else torch.float64
     mt = torch.as_tensor(m, dtype=dt, device="cuda").contiguous()
     dtn = torch.as_tensor(d, dtype=dt, device="cuda").contiguous()
     fwd = op.forward(mt)
@@ -42,7 +44,7 @@ def run(gm, w, prec, m, d):
     return out
 
 
-@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("prec", [1, 0, 2])
 def test_grav16_full_vs_oracle(gm, prec):
     w = W.WORKLOADS["grav16"]
     geom = geometry(w)
@@ -52,7 +54,7 @@ def test_grav16_full_vs_oracle(gm, prec):
     assert rel_err(tr, O.transpose(geom, d)) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("prec", [1, 0, 2])
 @pytest.mark.parametrize("seed", range(8))
 def test_random_small_shapes_vs_oracle(gm, prec, seed):
     """Odd, unequal, asymmetric-padded shapes (several tiles and ragged tails in every kernel)."""
@@ -77,7 +79,7 @@ EDGE = [
 ]
 
 
-@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("prec", [1, 0, 2])
 @pytest.mark.parametrize("w", EDGE, ids=[e.name for e in EDGE])
 def test_edge_shapes_vs_oracle(gm, prec, w):
     geom = geometry(w)
@@ -94,7 +96,7 @@ def test_variable_layer_depths_vs_oracle(gm):
 
     z = [2.0, 7.0, 20.0, 22.0, 60.0]
     geom = O.Geometry(9, 6, 4, 10.0, 15.0, tuple(z), 1, 2, 3, 0, O.MAGNETIC, 55.0, 12.0, 47000.0)
-    for prec, dt in ((gm.F64, torch.float64), (gm.F32, torch.float32)):
+    for prec, dt in ((gm.F64, torch.float64), (gm.F32, torch.float32), (gm.DF64, torch.float64)):
         op = gm.Operator(9, 6, 4, 10.0, 15.0, px=1, pxr=2, py=3, pyr=0, zplanes=z, kind=gm.MAGNETIC,
                          incl_deg=55.0, decl_deg=12.0, F_nT=47000.0, precision=prec)
         m = W.random_vector((4, 9, 12), 1)
@@ -111,7 +113,7 @@ def _golden(name):
 
 
 @pytest.mark.parametrize("name", ["mag64", "grav300", "mag128"])
-@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("prec", [1, 0, 2])
 def test_full_size_sampled_vs_oracle(gm, name, prec):
     """Full-size workloads, the launch configuration the benchmark uses, against oracle values
     at sampled stations and cells."""
@@ -154,7 +156,7 @@ def test_spectrum_is_fft_of_oracle_generator(gm):
     op.close()
 
 
-@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("prec", [1, 0, 2])
 def test_dot_product_adjoint(gm, prec):
     """<G m, d> = <m, G^T d> (Sec. 3: the transpose product uses the same spectra)."""
     import torch
@@ -167,7 +169,7 @@ def test_dot_product_adjoint(gm, prec):
     a = float((op.forward(m).double() * d.double()).sum())
     b = float((m.double() * op.transpose(d).double()).sum())
     scale = float(op.forward(m).double().norm() * d.double().norm())
-    assert abs(a - b) / scale < (1e-14 if prec == 1 else 1e-6)
+    assert abs(a - b) / scale < {1: 1e-14, 2: 1e-13, 0: 1e-6}[prec]
     op.close()
 
 
@@ -184,7 +186,7 @@ def test_linearity(gm):
     op.close()
 
 
-@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("prec", [1, 0, 2])
 def test_host_buffer_entry_points_match_device(gm, prec):
     import torch
 
@@ -258,7 +260,7 @@ def test_gravity_real_spectra_are_the_fft_of_the_oracle_generator(gm):
     op.close()
 
 
-@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("prec", [1, 0, 2])
 @pytest.mark.parametrize("name", ["grav16", "grav300", "grav64"])
 def test_gravity_real_spectra_match_complex_spectra(gm, monkeypatch, name, prec):
     """The real-spectrum path (one real x complex product per layer and the padding phase once)
@@ -273,8 +275,8 @@ def test_gravity_real_spectra_match_complex_spectra(gm, monkeypatch, name, prec)
     assert op.info.spectrum_real == 1
     op.close()
     got_f, got_t = run(gm, w, prec, m, d)
-    # FP64: the bound of the oracle gate (the 300x250x60 transpose is 8e-13 from the oracle itself)
-    tol = 1e-12 if prec == 1 else 2e-6
+    # FP64 / DF64: the bound of the oracle gate (the 300x250x60 transpose is 8e-13 from the oracle itself)
+    tol = 2e-6 if prec == 0 else 1e-12
     assert rel_err(got_f, ref_f) < tol
     assert rel_err(got_t, ref_t) < tol
 
@@ -288,7 +290,7 @@ def test_asymmetric_padding_and_magnetic_keep_complex_spectra(gm):
         op.close()
 
 
-@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("prec", [1, 0, 2])
 def test_host_entry_points_direct_and_staged_agree(gm, monkeypatch, prec):
     """Pinned buffers are used in place by the kernels; GM_HOST_STAGING=1 stages them through
     device memory; pageable buffers are always staged.  All three give the device result."""
@@ -316,3 +318,39 @@ def test_host_entry_points_direct_and_staged_agree(gm, monkeypatch, prec):
         op.transpose_host(di, om)
         assert torch.equal(od, ref_d) and torch.equal(om, ref_m), (pinned, staged)
     op.close()
+
+
+@pytest.mark.parametrize("name", ["mag64", "grav300", "mag128"])
+def test_df64_whole_vector_vs_fp64(gm, name):
+    """Double-float against the FP64 run over every element: FP32 pairs carry a 48-bit
+    significand, so the two differ by the rounding of a few hundred pair operations per output
+    (about 2^-47 each), far inside the FP64 oracle gate."""
+    w = W.WORKLOADS[name]
+    m, d = W.model(name, 0), W.data(name, 0)
+    f64, t64 = run(gm, w, 1, m, d)
+    fdf, tdf = run(gm, w, 2, m, d)
+    assert rel_err(fdf, f64) < 1e-13, rel_err(fdf, f64)
+    assert rel_err(tdf, t64) < 1e-13, rel_err(tdf, t64)
+
+
+@pytest.mark.parametrize("name", ["grav16", "mag64"])
+def test_df64_spectra_are_the_fp64_spectra_split(gm, name):
+    """Each stored double-float value is the FP64 set-up value rounded to an FP32 pair."""
+    w = W.WORKLOADS[name]
+    a = gm.Operator.from_workload(w, precision=gm.F64)
+    b = gm.Operator.from_workload(w, precision=gm.DF64)
+    assert (a.info.spectrum_real, a.info.spectrum_bytes) == (b.info.spectrum_real, b.info.spectrum_bytes)
+    s64, sdf = a.spectrum(), b.spectrum()
+    assert np.max(np.abs(sdf - s64)) <= 2.0 ** -47 * np.max(np.abs(s64))
+    a.close()
+    b.close()
+
+
+def test_df64_needs_register_codelet_lengths(gm, monkeypatch):
+    """Lengths off the ladder (here N'x = 1200 > 1024) have no double-float kernels: set-up
+    reports GM_EINVAL instead of falling back."""
+    with pytest.raises(gm.GravMagError, match="GM_DF64"):
+        gm.Operator(600, 4, 1, 10.0, 10.0, 10.0, precision=gm.DF64)
+    monkeypatch.setenv("GM_GENERIC_FFT", "1")
+    with pytest.raises(gm.GravMagError, match="GM_DF64"):
+        gm.Operator(16, 16, 2, 10.0, 10.0, 10.0, precision=gm.DF64)
