@@ -336,7 +336,8 @@ def codelet(n, inverse, nin=None):
 
 # input-pruned variants: sizes used as the first pass of zero-padded transforms, with the
 # numbers of leading nonzero inputs offered (a kernel picks the smallest bucket that covers it)
-# (none instantiated: for the prime-radix codelets used here the saving is ~5%)
+# (none instantiated: in a trial the pruned first passes saved about 5% of the arithmetic of the
+# prime-radix codelets and ran slower than the full codelets)
 PRUNED = {}
 
 
