@@ -374,7 +374,8 @@ def selftest():
     return worst
 
 
-def main():
+def render() -> str:
+    """The text of gm_fft_codelets.cuh."""
     parts = ["// gm_fft_codelets.cuh -- GENERATED by gen_fft_codelets.py; do not edit by hand.",
              "// Straight-line in-register DFTs, natural order: dftN (forward, exp(-2 pi i nk/N)) and",
              "// idftN (inverse, exp(+2 pi i nk/N), unnormalised), for C = float2 or double2.",
@@ -402,9 +403,13 @@ def main():
                 parts.append(f"template <> struct DftIn<{n}, {L}, {'true' if inv else 'false'}> {{ template <typename C> "
                              f"__device__ __forceinline__ static void run(C (&v)[{n}]) {{ {nm}(v); }} }};")
     parts += ["", "}  // namespace cl", "}  // namespace gm", ""]
+    return "\n".join(parts)
+
+
+def main():
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "gm_fft_codelets.cuh")
     with open(out, "w") as f:
-        f.write("\n".join(parts))
+        f.write(render())
     print(out)
 
 
