@@ -114,7 +114,12 @@ cudaError_t make_twiddles(int N, int precision, void **dev_out) {
     }
     cudaError_t err = cudaMalloc(dev_out, elt * (size_t)N);
     if (err != cudaSuccess) return err;
-    return cudaMemcpy(*dev_out, host.data(), elt * (size_t)N, cudaMemcpyHostToDevice);
+    err = cudaMemcpy(*dev_out, host.data(), elt * (size_t)N, cudaMemcpyHostToDevice);
+    // A copy from pageable host memory may return before the data reaches the device, and it
+    // is ordered only on the legacy default stream: the set-up kernels run on a non-blocking
+    // stream and callers may apply on any stream, so wait for the table to land.
+    if (err == cudaSuccess) err = cudaDeviceSynchronize();
+    return err;
 }
 
 }  // namespace gm
@@ -334,6 +339,8 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
     if (ncount) {
         SETUP_TRY(cudaMalloc(&p->work_counters, sizeof(unsigned int) * ncount), "workspace");
         SETUP_TRY(cudaMemset(p->work_counters, 0, sizeof(unsigned int) * ncount), "workspace");
+        // the memset is ordered on the legacy default stream only; applies may come on any stream
+        SETUP_TRY(cudaDeviceSynchronize(), "workspace");
     }
     SETUP_TRY(cudaMalloc(&p->stage_m, rel * n_model), "staging");
     SETUP_TRY(cudaMalloc(&p->stage_d, rel * n_data), "staging");

@@ -47,7 +47,7 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 
 // part[blk] = partial SUM a[i]^2 (i < na); part[kRedBlocks + blk] = partial SUM b[i]^2 (i < nb)
 template <typename R>
-__global__ void k_sumsq2(const R *__restrict__ a, size_t na, const R *__restrict__ b, size_t nb, double *part) {
+__global__ void k_sumsq2(const R *a, size_t na, const R *b, size_t nb, double *part) {
     pdl_wait();
     pdl_trigger();
     __shared__ double sh[32];
@@ -128,7 +128,7 @@ inline double cgls_tol2(int precision) {
 
 // r = d - r (r holds G x0 on entry)
 template <typename R>
-__global__ void k_residual0(const R *__restrict__ d, R *__restrict__ r, size_t m) {
+__global__ void k_residual0(const R *d, R *r, size_t m) {
     pdl_wait();
     pdl_trigger();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
@@ -137,7 +137,7 @@ __global__ void k_residual0(const R *__restrict__ d, R *__restrict__ r, size_t m
 
 // s -= alpha^2 x; p = s (when set_p)
 template <typename R>
-__global__ void k_s_update(R *__restrict__ s, const R *__restrict__ x, R *__restrict__ p, size_t n, R a2, int set_p) {
+__global__ void k_s_update(R *s, const R *x, R *p, size_t n, R a2, int set_p) {
     pdl_wait();
     pdl_trigger();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -149,8 +149,8 @@ __global__ void k_s_update(R *__restrict__ s, const R *__restrict__ x, R *__rest
 
 // x += a p (i < n); r -= a q (i < m)
 template <typename R>
-__global__ void k_update_xr(R *__restrict__ x, const R *__restrict__ p, size_t n, R *__restrict__ r,
-                            const R *__restrict__ q, size_t m, const double *sc) {
+__global__ void k_update_xr(R *x, const R *p, size_t n, R *r,
+                            const R *q, size_t m, const double *sc) {
     pdl_wait();
     pdl_trigger();
     const R a = (R)sc[S_A];
@@ -162,7 +162,7 @@ __global__ void k_update_xr(R *__restrict__ x, const R *__restrict__ p, size_t n
 
 // p = s + b p
 template <typename R>
-__global__ void k_update_p(R *__restrict__ p, const R *__restrict__ s, size_t n, const double *sc) {
+__global__ void k_update_p(R *p, const R *s, size_t n, const double *sc) {
     pdl_wait();
     pdl_trigger();
     const R b = (R)sc[S_B];

@@ -14,7 +14,10 @@ namespace gm {
 // kernel on the stream has finished.  pdl_wait() blocks until that kernel has completed and its
 // memory is visible (a no-op under a normal launch); a kernel calls it before its first access to
 // data another kernel writes or reads.  pdl_trigger() lets the next kernel be scheduled once every
-// block of this one has passed it.
+// block of this one has passed it.  The wait orders only what the compiler cannot move above it:
+// data written by earlier kernels is read after it with volatile coherent loads, or through
+// pointers without __restrict__ (a const __restrict__ pointer lets the compiler use non-coherent
+// loads and schedule them before the wait).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 

@@ -103,14 +103,50 @@ __device__ __forceinline__ dfc ld_nc(const dfc *p) {
     asm("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.h.x), "=f"(v.h.y), "=f"(v.l.x), "=f"(v.l.y) : "l"(p));
     return v;
 }
-// load cached in L2 only (values other blocks of the same kernel wrote)
-__device__ __forceinline__ float2 ld_cg(const float2 *p) { return __ldcg(p); }
-__device__ __forceinline__ double2 ld_cg(const double2 *p) { return __ldcg(p); }
+// Coherent loads cached in L2 only, for data another kernel (or another block of this one) wrote:
+// the intermediates of the previous kernel in the stream, read after pdl_wait(), and the partial
+// sums of other blocks.  They are volatile asm so that the compiler keeps them after pdl_wait()
+// (a load through a const __restrict__ pointer may otherwise become a non-coherent load that is
+// scheduled before the wait, and read the buffer before the previous kernel has written it).
+__device__ __forceinline__ float2 ld_cg(const float2 *p) {
+    float2 v;
+    asm volatile("ld.global.cg.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double2 ld_cg(const double2 *p) {
+    double2 v;
+    asm volatile("ld.global.cg.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
 __device__ __forceinline__ dfc ld_cg(const dfc *p) {
     dfc v;
     asm volatile("ld.global.cg.v4.f32 {%0, %1, %2, %3}, [%4];"
                  : "=f"(v.h.x), "=f"(v.h.y), "=f"(v.l.x), "=f"(v.l.y)
                  : "l"(p));
+    return v;
+}
+// The same load predicated on ok (no access when ok is false); the value is zero then.
+__device__ __forceinline__ float2 ld_cg_if(const float2 *p, bool ok) {
+    float2 v = make_float2(0.f, 0.f);
+    asm volatile("{ .reg .pred q; setp.ne.b32 q, %3, 0; @q ld.global.cg.v2.f32 {%0, %1}, [%2]; }"
+                 : "+f"(v.x), "+f"(v.y)
+                 : "l"(p), "r"((int)ok));
+    return v;
+}
+__device__ __forceinline__ double2 ld_cg_if(const double2 *p, bool ok) {
+    double2 v = make_double2(0.0, 0.0);
+    asm volatile("{ .reg .pred q; setp.ne.b32 q, %3, 0; @q ld.global.cg.v2.f64 {%0, %1}, [%2]; }"
+                 : "+d"(v.x), "+d"(v.y)
+                 : "l"(p), "r"((int)ok));
+    return v;
+}
+__device__ __forceinline__ dfc ld_cg_if(const dfc *p, bool ok) {
+    dfc v;
+    v.h = make_float2(0.f, 0.f);
+    v.l = make_float2(0.f, 0.f);
+    asm volatile("{ .reg .pred q; setp.ne.b32 q, %5, 0; @q ld.global.cg.v4.f32 {%0, %1, %2, %3}, [%4]; }"
+                 : "+f"(v.h.x), "+f"(v.h.y), "+f"(v.l.x), "+f"(v.l.y)
+                 : "l"(p), "r"((int)ok));
     return v;
 }
 __device__ __forceinline__ void st_hint(float2 *p, float2 v, uint64_t pol) {
@@ -304,7 +340,7 @@ __global__ void __launch_bounds__(THREADS) k_rows_c2r(const C *__restrict__ in, 
             const int it = threadIdx.x + b * THREADS;
             const int k = it / (2 * PAIRS), row = it - k * 2 * PAIRS;
             const int q = q0 + row;
-            tmp[b] = (it < TOT && q < rows) ? in[k * ld_k + layer * ld_layer + q * ld_row] : c_make<C>(0, 0);
+            tmp[b] = ld_cg_if(in + (k * ld_k + layer * ld_layer + q * ld_row), it < TOT && q < rows);
         }
 #pragma unroll
         for (int b = 0; b < BATCH; ++b) {
@@ -457,7 +493,7 @@ __global__ void __launch_bounds__(THREADS)
 #pragma unroll
             for (int rr = 0; rr < R1; ++rr) {
                 const int q = j + R2 * rr;
-                v[rr] = (valid && q < ny) ? col[q] : c_make<C>(0, 0);
+                v[rr] = ld_cg_if(col + q, valid && q < ny);
             }
             pass1_store<R1, false>(v, ex + (c * LSTEP + l) * EX, j);
         }
@@ -564,7 +600,7 @@ __global__ void __launch_bounds__(THREADS)
 #pragma unroll
         for (int rr = 0; rr < R1; ++rr) {
             const int q = j + R2 * rr;
-            v[rr] = (kx < Kx && q < sy) ? col[q] : c_make<C>(0, 0);
+            v[rr] = ld_cg_if(col + q, kx < Kx && q < sy);
         }
         pass1_store<R1, false>(v, ex + c * EXM, j);
     }

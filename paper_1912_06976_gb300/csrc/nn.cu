@@ -1120,8 +1120,9 @@ gm_status gm_net_set_params(gm_net_handle net, const float *host, int64_t n, int
     cudaError_t e = cudaMemcpy(dst, host, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && which == 0) {
         gm::nn::k_pack_weights<<<grid1(net->nparam), 256>>>(net->w, net->wf, net->wd, net->pack);
-        e = cudaDeviceSynchronize();
     }
+    // a copy from pageable memory may return before it lands; later work may come on any stream
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return e == cudaSuccess ? GM_OK : nn_fail(GM_ECUDA, cudaGetErrorString(e));
 }
 
