@@ -208,6 +208,19 @@ def cpu_oracle_sample(w, budget_s: float = 12.0, min_batches: int = 1, per_threa
             "seconds": t_total}
 
 
+def cpu_oracle_one_core(w, budget_s: float = 3.0):
+    """The same sampled-entry timing of the oracle on one host thread (a shorter sample)."""
+    import oracle as O
+
+    n = O.threads()
+    O.set_threads(1)
+    try:
+        r = cpu_oracle_sample(w, budget_s=budget_s, per_thread=256, seed=4321)
+    finally:
+        O.set_threads(n)
+    return {"value_1core": r["value"], "sample_1core": r["sample"]}
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank, world, _ = dist_env()
@@ -485,9 +498,11 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(w)
         cpu.pop("seconds", None)
+        cpu.update(cpu_oracle_one_core(w))
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+                "ms_per_step_median": statistics.median(per_step), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {**workload_config(w, inf), "parallelism": f"replicas{world}" if world > 1 else "1 GPU",
                            "timing": timing_mode},
