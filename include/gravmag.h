@@ -103,7 +103,10 @@ typedef struct {
  * FFTs.  nx, ny are the STATION counts s_x, s_y (= unpadded cells); px, py
  * pad cells on EACH side; dz the uniform layer thickness; kind a gm_kind;
  * incl_deg, decl_deg are ignored for gravity.  F = 50000 nT, FP32 applies.
- * Returns NULL on error (see gm_last_status / gm_last_error). */
+ * Set-up blocks the calling thread and synchronises the current device: when
+ * it returns, every table and spectrum is on the device, so the handle can be
+ * used on any stream.  Returns NULL on error (see gm_last_status /
+ * gm_last_error). */
 GM_API gm_handle grav_mag_setup(int nx, int ny, int nz, double dx, double dy, double dz, int px, int py,
                          int kind, double incl_deg, double decl_deg);
 
