@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
 and ``bench.py``'s CPU-baseline leg, never by the product package.  The
-arithmetic lives in ``gm_oracle.c`` (long double, dense G entry by entry from
+arithmetic lives in ``gm_oracle.c`` (IEEE binary128, dense G entry by entry from
 the prism formulas of Sec. 4 of Hogue, Renaut & Vatankhah, arXiv 1912.06976);
 this module only builds that file with gcc and marshals numpy arrays through
 ctypes.
@@ -38,16 +38,25 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile gm_oracle.c into oracle/_build/libgm_oracle.so (gcc, OpenMP if available)."""
+    """Compile gm_oracle.c into oracle/_build/libgm_oracle.so (gcc, OpenMP if available).
+
+    The arithmetic is binary128: long double where that is the format (aarch64), else
+    __float128 with libquadmath (x86-64); gcc fails on a machine with neither.
+    """
     os.makedirs(_BUILD, exist_ok=True)
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     base = ["gcc", "-O2", "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC, "-lm"]
-    try:
-        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
-    except subprocess.CalledProcessError:
-        subprocess.run(base, check=True, capture_output=True)
+    last = None
+    for extra_pre, extra_post in ((["-fopenmp"], ["-lquadmath"]), (["-fopenmp"], []), ([], ["-lquadmath"]), ([], [])):
+        try:
+            subprocess.run(base[:1] + extra_pre + base[1:] + extra_post, check=True, capture_output=True, text=True)
+            break
+        except subprocess.CalledProcessError as e:
+            last = e
+    else:
+        raise RuntimeError(f"cannot build the oracle: {last.stderr if last else ''}")
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -90,7 +99,7 @@ def _load():
         lib.gmo_transpose.argtypes = [gp, dp, i64p, ctypes.c_int64, dp]
         lib.gmo_threads.restype = ctypes.c_int
         lib.gmo_set_threads.argtypes = [ctypes.c_int]
-        lib.gmo_ld_mant_dig.restype = ctypes.c_int
+        lib.gmo_mant_dig.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -215,7 +224,7 @@ def dense(geom: Geometry) -> np.ndarray:
 
 
 def forward(geom: Geometry, m, stations=None) -> np.ndarray:
-    """d = G m (all stations, or the listed ones), summed in long double."""
+    """d = G m (all stations, or the listed ones), summed in binary128."""
     mm = np.ascontiguousarray(m, dtype=np.float64).reshape(-1)
     assert mm.size == geom.n
     g, _z = geom._c()
@@ -230,7 +239,7 @@ def forward(geom: Geometry, m, stations=None) -> np.ndarray:
 
 
 def transpose(geom: Geometry, d, cells=None) -> np.ndarray:
-    """m' = G^T d (all cells, or the listed ones), summed in long double."""
+    """m' = G^T d (all cells, or the listed ones), summed in binary128."""
     dd = np.ascontiguousarray(d, dtype=np.float64).reshape(-1)
     assert dd.size == geom.m
     g, _z = geom._c()
@@ -252,6 +261,6 @@ def set_threads(n: int) -> None:
     _load().gmo_set_threads(int(n))
 
 
-def long_double_digits() -> int:
-    """Significand bits of the C long double the oracle runs in (64 on x86-64, 113 on aarch64)."""
-    return _load().gmo_ld_mant_dig()
+def significand_bits() -> int:
+    """Significand bits of the arithmetic the oracle runs in (113: IEEE binary128)."""
+    return _load().gmo_mant_dig()

@@ -14,10 +14,15 @@
  * circulant or FFT code here, no corner-grid reuse and no reordering: every
  * entry is evaluated from its own 8 corners.
  *
- * Arithmetic is long double (x87 80-bit on x86-64, IEEE binary128 on
- * aarch64) with the stable forms of the logarithms described below, so the
- * rounding of this code sits well below the 1e-12 gate the FP64 GPU path is
- * held to.
+ * Arithmetic is IEEE binary128 (113-bit significand): long double on
+ * aarch64, __float128 with libquadmath on x86-64 (where long double is only
+ * the 64-bit-significand x87 format); the build refuses any other format.
+ * Far from the station the 8 corner terms of an entry cancel: their size is
+ * about r ln r while the entry is about dx dy dz z / r^3, a ratio near 4e11
+ * for a 20 m top-layer cell 7.8 km away.  In binary128 (eps = 1.9e-34) that
+ * cancellation leaves about 1e-22 relative error, far below the 1e-12 gate
+ * the FP64 GPU path is held to; the x87 format (eps = 1.1e-19) would leave
+ * up to 1e-7 at such entries, which is why it is not used.
  *
  * Geometry (0-based; Sec. 2.1.1-2.1.2, Eq. PaddedDistances and the notation
  * table of App. A):
@@ -66,7 +71,28 @@
 #include <omp.h>
 #endif
 
-typedef long double ld;
+#if LDBL_MANT_DIG == 113
+typedef long double ld; /* IEEE binary128 */
+#define LDC(x) x##L
+#define ld_log logl
+#define ld_atan atanl
+#define ld_sqrt sqrtl
+#define ld_cos cosl
+#define ld_sin sinl
+#define GMO_MANT_DIG LDBL_MANT_DIG
+#elif defined(__SIZEOF_FLOAT128__)
+#include <quadmath.h>
+typedef __float128 ld; /* IEEE binary128 in software */
+#define LDC(x) x##Q
+#define ld_log logq
+#define ld_atan atanq
+#define ld_sqrt sqrtq
+#define ld_cos cosq
+#define ld_sin sinq
+#define GMO_MANT_DIG FLT128_MANT_DIG
+#else
+#error "the oracle needs IEEE binary128 arithmetic (long double on aarch64 or __float128)"
+#endif
 
 #define GMO_GRAVITY 0
 #define GMO_MAGNETIC 1
@@ -81,22 +107,22 @@ typedef struct {
     double incl_deg, decl_deg, F_nT;
 } gmo_geom;
 
-static const ld GMO_GAMMA = 6.67430e-3L; /* mGal per (g/cm^3 * m) */
-static const ld GMO_PI = 3.14159265358979323846264338327950288L;
+static const ld GMO_GAMMA = LDC(6.67430e-3); /* mGal per (g/cm^3 * m) */
+static const ld GMO_PI = LDC(3.14159265358979323846264338327950288);
 
 /* ln(rho + a) where rho = sqrt(a^2 + b2), b2 = sum of the squares of the
  * two other coordinates.  For a < 0 the sum is rewritten as b2 / (rho - a). */
 static ld ln_rho_plus(ld a, ld b2, ld rho) {
-    if (a >= 0.0L) return logl(rho + a);
-    return logl(b2 / (rho - a));
+    if (a >= LDC(0.0)) return ld_log(rho + a);
+    return ld_log(b2 / (rho - a));
 }
 
 /* The gravity corner function of Sec. 4.1 at one corner. */
 static ld grav_corner(ld x, ld y, ld z) {
     ld x2 = x * x, y2 = y * y, z2 = z * z;
-    ld rho = sqrtl(x2 + y2 + z2);
-    ld t = 0.0L;
-    if (z != 0.0L) t = z * atanl((x * y) / (z * rho));
+    ld rho = ld_sqrt(x2 + y2 + z2);
+    ld t = LDC(0.0);
+    if (z != LDC(0.0)) t = z * ld_atan((x * y) / (z * rho));
     return t - x * ln_rho_plus(y, x2 + z2, rho) - y * ln_rho_plus(x, y2 + z2, rho);
 }
 
@@ -105,12 +131,12 @@ static ld grav_corner(ld x, ld y, ld z) {
  * limits carry +, so a prism below the station gives a positive value. */
 static ld grav_prism_ld(ld x1, ld x2, ld y1, ld y2, ld z1, ld z2) {
     const ld xs[2] = {x1, x2}, ys[2] = {y1, y2}, zs[2] = {z1, z2};
-    ld s = 0.0L;
+    ld s = LDC(0.0);
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             for (int c = 0; c < 2; ++c) {
                 int lower = (a == 0) + (b == 0) + (c == 0);
-                ld mu = (lower & 1) ? -1.0L : 1.0L;
+                ld mu = (lower & 1) ? -LDC(1.0) : LDC(1.0);
                 s += mu * grav_corner(xs[a], ys[b], zs[c]);
             }
     return s;
@@ -130,17 +156,17 @@ static void mag_terms_ld(ld x1, ld x2, ld y1, ld y2, ld z1, ld z2, ld out[6]) {
         for (int b = 0; b < 2; ++b)
             for (int c = 0; c < 2; ++c) {
                 int lower = (a == 0) + (b == 0) + (c == 0);
-                ld mu = (lower & 1) ? -1.0L : 1.0L;
+                ld mu = (lower & 1) ? -LDC(1.0) : LDC(1.0);
                 ld x = xs[a], y = ys[b], z = zs[c];
                 ld x2 = x * x, y2 = y * y, z2 = z * z;
-                ld rho = sqrtl(x2 + y2 + z2);
+                ld rho = ld_sqrt(x2 + y2 + z2);
                 Lx += mu * ln_rho_plus(x, y2 + z2, rho);
                 Ly += mu * ln_rho_plus(y, x2 + z2, rho);
                 Lz += mu * ln_rho_plus(z, x2 + y2, rho);
-                Ax += mu * atanl((y * z) / (x * rho));
-                Ay += mu * atanl((x * z) / (y * rho));
-                if (z != 0.0L) Az += mu * atanl((x * y) / (z * rho));
-                else Az += mu * (((x * y) > 0.0L) ? GMO_PI / 2 : -GMO_PI / 2);
+                Ax += mu * ld_atan((y * z) / (x * rho));
+                Ay += mu * ld_atan((x * z) / (y * rho));
+                if (z != LDC(0.0)) Az += mu * ld_atan((x * y) / (z * rho));
+                else Az += mu * (((x * y) > LDC(0.0)) ? GMO_PI / 2 : -GMO_PI / 2);
             }
     out[0] = Lx; out[1] = Ly; out[2] = Lz; out[3] = Ax; out[4] = Ay; out[5] = Az;
 }
@@ -155,12 +181,12 @@ void gmo_prism_mag_terms(double x1, double x2, double y1, double y2, double z1, 
 /* The five coefficients of Eq. magnetickernel (already multiplied by F/4pi),
  * in the order of the terms {L_x, L_y, L_z, A_x, A_y}. */
 static void mag_coeffs(const gmo_geom *g, ld c[5]) {
-    ld I = (ld)g->incl_deg * GMO_PI / 180.0L, D = (ld)g->decl_deg * GMO_PI / 180.0L;
-    ld l = cosl(I) * cosl(D), m = cosl(I) * sinl(D), n = sinl(I);
-    ld H = (ld)g->F_nT / (4.0L * GMO_PI);
-    c[0] = H * 2.0L * m * n;     /* L_x: T_yz */
-    c[1] = H * 2.0L * l * n;     /* L_y: T_xz */
-    c[2] = H * 2.0L * l * m;     /* L_z: T_xy */
+    ld I = (ld)g->incl_deg * GMO_PI / LDC(180.0), D = (ld)g->decl_deg * GMO_PI / LDC(180.0);
+    ld l = ld_cos(I) * ld_cos(D), m = ld_cos(I) * ld_sin(D), n = ld_sin(I);
+    ld H = (ld)g->F_nT / (LDC(4.0) * GMO_PI);
+    c[0] = H * LDC(2.0) * m * n;     /* L_x: T_yz */
+    c[1] = H * LDC(2.0) * l * n;     /* L_y: T_xz */
+    c[2] = H * LDC(2.0) * l * m;     /* L_z: T_xy */
     c[3] = H * (n * n - l * l);  /* A_x: -T_xx + T_zz share */
     c[4] = H * (n * n - m * m);  /* A_y: -T_yy + T_zz share */
 }
@@ -173,9 +199,9 @@ void gmo_mag_coeffs(const gmo_geom *g, double out[5]) {
 
 /* Entry G[k, l] with k = j*sx + i and l = (r*ny + q)*nx + p. */
 static ld entry_ld(const gmo_geom *g, const ld mc[5], int i, int j, int p, int q, int r) {
-    ld x1 = ((ld)(p - i - g->pxl) - 0.5L) * (ld)g->dx;
+    ld x1 = ((ld)(p - i - g->pxl) - LDC(0.5)) * (ld)g->dx;
     ld x2 = x1 + (ld)g->dx;
-    ld y1 = ((ld)(q - j - g->pyl) - 0.5L) * (ld)g->dy;
+    ld y1 = ((ld)(q - j - g->pyl) - LDC(0.5)) * (ld)g->dy;
     ld y2 = y1 + (ld)g->dy;
     ld z1 = (ld)g->zplanes[r];
     ld z2 = (ld)g->zplanes[r + 1];
@@ -226,7 +252,7 @@ void gmo_entries(const gmo_geom *g, const int64_t *stations, const int64_t *cell
 }
 
 /* d[k] = SUM_l G[k, l] m[l] for the stations listed in rows (all stations
- * when rows == NULL, in which case nrows must be sx*sy).  Sums in long double. */
+ * when rows == NULL, in which case nrows must be sx*sy).  Sums in binary128. */
 void gmo_forward(const gmo_geom *g, const double *m, const int64_t *rows, int64_t nrows,
                  double *d) {
     const int nx = gmo_nx(g), ny = gmo_ny(g);
@@ -236,7 +262,7 @@ void gmo_forward(const gmo_geom *g, const double *m, const int64_t *rows, int64_
     for (int64_t t = 0; t < nrows; ++t) {
         int64_t k = rows ? rows[t] : t;
         int i = (int)(k % g->sx), j = (int)(k / g->sx);
-        ld acc = 0.0L;
+        ld acc = LDC(0.0);
         for (int r = 0; r < g->nz; ++r)
             for (int q = 0; q < ny; ++q)
                 for (int p = 0; p < nx; ++p)
@@ -258,7 +284,7 @@ void gmo_transpose(const gmo_geom *g, const double *d, const int64_t *cols, int6
         int p = (int)(l % nx);
         int q = (int)((l / nx) % ny);
         int r = (int)(l / ((int64_t)nx * ny));
-        ld acc = 0.0L;
+        ld acc = LDC(0.0);
         for (int j = 0; j < g->sy; ++j)
             for (int i = 0; i < g->sx; ++i)
                 acc += entry_ld(g, mc, i, j, p, q, r) * (ld)d[(int64_t)j * g->sx + i];
@@ -283,5 +309,6 @@ void gmo_set_threads(int n) {
 #endif
 }
 
-/* Size of long double's significand, so tests can state which format ran. */
-int gmo_ld_mant_dig(void) { return LDBL_MANT_DIG; }
+/* Significand bits of the arithmetic type (113 for binary128), so tests and
+ * stored samples can state which format ran. */
+int gmo_mant_dig(void) { return GMO_MANT_DIG; }

@@ -24,7 +24,8 @@ from paper_1912_06976_gb300 import workloads as W  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
-SAMPLES = {"mag64": (24, 24), "grav300": (12, 24), "mag128": (16, 24)}
+# (stations for d = G m, cells for m' = G^T d) per workload: 64 of each
+SAMPLES = {"mag64": (64, 64), "grav300": (64, 64), "mag128": (64, 64)}
 
 
 def geometry(w):
@@ -40,6 +41,10 @@ def sample_indices(n, k, tag):
 
 
 def make(name):
+    bits = O.significand_bits()
+    if bits != 113:
+        # far-field entries lose up to 1e-7 of their value in a 64-bit significand
+        raise SystemExit(f"the oracle runs in a {bits}-bit significand; stored samples need binary128 (113)")
     w = W.WORKLOADS[name]
     geom = geometry(w)
     kf, kt = SAMPLES[name]
@@ -59,9 +64,9 @@ def make(name):
         "forward": [float(v) for v in fwd],
         "transpose_cells": ti.tolist(),
         "transpose": [float(v) for v in tr],
-        "oracle_long_double_bits": O.long_double_digits(),
+        "oracle_significand_bits": bits,
         "note": "d = G m at the listed stations and m' = G^T d at the listed cells, "
-                "m = workloads.model(name, 0), d = workloads.data(name, 0), by oracle/gm_oracle.c",
+                "m = workloads.model(name, 0), d = workloads.data(name, 0), by oracle/gm_oracle.c in IEEE binary128",
     }
     path = os.path.join(HERE, f"sampled_{name}.json")
     with open(path, "w") as f:

@@ -181,6 +181,140 @@ def test_magnetic_entries_match_quadrature(incl, decl):
         checked += 1
 
 
+# ---------------------------------------------------------------- far field: rounding of the corner sums
+# Far from the station the 8 corner terms of an entry are about r ln r (gravity) or ln r
+# (magnetic) while the entry is about V z / r^3: on the 300 x 250 x 60 grid the top-layer
+# terms cancel by a factor near 5e11, so an oracle in a 64-bit significand (x87) is off by up
+# to 1e-7 there.  These pins hold the oracle to 1e-15 at the farthest offsets of the two largest
+# grids, against the same signed corner sum in 50-digit arithmetic and, independently of the
+# corner formula, against Gauss-Legendre quadrature of the integrand in 30-digit arithmetic.
+FAR_GRAV = O.Geometry.uniform(300, 250, 60, 20.0, 20.0, 20.0, 30, 25)  # 10 % padding per side
+FAR_MAG = O.Geometry.uniform(128, 128, 32, 25.0, 25.0, 25.0, 0, 0, O.MAGNETIC, 60.0, 0.0)
+FAR_MAG_D = O.Geometry.uniform(64, 64, 16, 25.0, 25.0, 25.0, 3, 3, O.MAGNETIC, 50.0, 8.0)
+# (station i, j, cell p, q, r): corners of the grid, the deepest layer, and offsets in between
+FAR_G_CASES = [(0, 0, 359, 299, 0), (0, 0, 359, 0, 0), (0, 0, 0, 299, 0), (299, 249, 0, 0, 0),
+               (0, 0, 359, 299, 59), (150, 100, 330, 280, 0), (0, 249, 359, 0, 30), (299, 0, 0, 299, 1),
+               (0, 0, 30, 299, 0)]
+FAR_M_CASES = [(0, 0, 127, 127, 0), (127, 0, 0, 127, 0), (0, 0, 127, 0, 5), (64, 64, 0, 127, 31)]
+FAR_MD_CASES = [(0, 0, 69, 69, 0), (63, 0, 0, 69, 0), (0, 63, 69, 0, 15)]
+
+
+def _corners_mp(geom, i, j, p, q, r):
+    """Exact corner offsets of cell (p, q, r) from station (i, j) as mpmath numbers."""
+    import mpmath as mp
+
+    x1 = (mp.mpf(p - i - geom.pxl) - mp.mpf(1) / 2) * mp.mpf(geom.dx)
+    y1 = (mp.mpf(q - j - geom.pyl) - mp.mpf(1) / 2) * mp.mpf(geom.dy)
+    return ((x1, x1 + mp.mpf(geom.dx)), (y1, y1 + mp.mpf(geom.dy)),
+            (mp.mpf(geom.zplanes[r]), mp.mpf(geom.zplanes[r + 1])))
+
+
+def _grav_corner_sum_mp(xs, ys, zs):
+    """gamma-free gravity entry as the signed corner sum of Sec. 4.1, plain form."""
+    import mpmath as mp
+
+    s = mp.mpf(0)
+    for a in range(2):
+        for b in range(2):
+            for c in range(2):
+                x, y, z = xs[a], ys[b], zs[c]
+                rho = mp.sqrt(x * x + y * y + z * z)
+                t = z * mp.atan(x * y / (z * rho)) if z != 0 else mp.mpf(0)
+                f = t - x * mp.log(rho + y) - y * mp.log(rho + x)
+                s += f if (a + b + c) % 2 == 1 else -f
+    return s
+
+
+def _mag_corner_sum_mp(xs, ys, zs, coef):
+    """Magnetic entry as the five signed corner sums of Sec. 4.2 with the derived coefficients."""
+    import mpmath as mp
+
+    L = [mp.mpf(0)] * 5
+    for a in range(2):
+        for b in range(2):
+            for c in range(2):
+                x, y, z = xs[a], ys[b], zs[c]
+                rho = mp.sqrt(x * x + y * y + z * z)
+                mu = 1 if (a + b + c) % 2 == 1 else -1
+                terms = (mp.log(rho + x), mp.log(rho + y), mp.log(rho + z),
+                         mp.atan(y * z / (x * rho)), mp.atan(x * z / (y * rho)))
+                L = [L[k] + mu * terms[k] for k in range(5)]
+    return sum(coef[k] * L[k] for k in range(5))
+
+
+def _mag_coef_mp(geom):
+    import mpmath as mp
+
+    I, D = mp.radians(geom.incl_deg), mp.radians(geom.decl_deg)
+    l, m, n = mp.cos(I) * mp.cos(D), mp.cos(I) * mp.sin(D), mp.sin(I)
+    H = mp.mpf(geom.F_nT) / (4 * mp.pi)
+    return [H * 2 * m * n, H * 2 * l * n, H * 2 * l * m, H * (n * n - l * l), H * (n * n - m * m)]
+
+
+def test_far_field_entries_match_50_digit_corner_sums():
+    """The oracle's far-field entries agree with the same corner sums in 50-digit arithmetic."""
+    import mpmath as mp
+
+    assert O.significand_bits() == 113
+    with mp.workdps(50):
+        gamma = mp.mpf("6.67430e-3")
+        for c in FAR_G_CASES:
+            ref = gamma * _grav_corner_sum_mp(*_corners_mp(FAR_GRAV, *c))
+            got = O.entry(FAR_GRAV, *c)
+            assert abs(got - ref) <= 1e-15 * abs(ref), (c, got, ref)
+        for geom, cases in ((FAR_MAG, FAR_M_CASES), (FAR_MAG_D, FAR_MD_CASES)):
+            coef = _mag_coef_mp(geom)
+            for c in cases:
+                ref = _mag_corner_sum_mp(*_corners_mp(geom, *c), coef)
+                got = O.entry(geom, *c)
+                assert abs(got - ref) <= 1e-15 * abs(ref), (c, got, ref)
+
+
+def _gl3_mp(f, bounds, n=6):
+    """Tensor Gauss-Legendre integral of f over a box in the current mpmath precision."""
+    import mpmath as mp
+
+    X, W = mp.mp.gauss_quadrature(n, "legendre")
+    (x1, x2), (y1, y2), (z1, z2) = bounds
+    hx, hy, hz = (x2 - x1) / 2, (y2 - y1) / 2, (z2 - z1) / 2
+    cx, cy, cz = (x2 + x1) / 2, (y2 + y1) / 2, (z2 + z1) / 2
+    tot = mp.mpf(0)
+    for a in range(n):
+        for b in range(n):
+            for c in range(n):
+                tot += W[a] * W[b] * W[c] * f(cx + hx * X[a], cy + hy * X[b], cz + hz * X[c])
+    return tot * hx * hy * hz
+
+
+def test_far_field_entries_match_quadrature_of_the_integrand():
+    """Independently of the corner formula: far-field entries equal the quadrature of
+    gamma z / r^3 (gravity) and of (F/4pi) F^.(grad grad 1/r).F^ (magnetic) to 1e-14; six nodes
+    per axis are exact to ~(cell / 2r)^12 there."""
+    import mpmath as mp
+
+    with mp.workdps(30):
+        gamma = mp.mpf("6.67430e-3")
+        grav = lambda x, y, z: z / mp.sqrt(x * x + y * y + z * z) ** 3  # noqa: E731
+        for c in FAR_G_CASES[:6]:
+            ref = gamma * _gl3_mp(grav, _corners_mp(FAR_GRAV, *c))
+            got = O.entry(FAR_GRAV, *c)
+            assert abs(got - ref) <= 1e-14 * abs(ref), (c, got, ref)
+        for geom, cases in ((FAR_MAG, FAR_M_CASES), (FAR_MAG_D, FAR_MD_CASES)):
+            I, D = mp.radians(geom.incl_deg), mp.radians(geom.decl_deg)
+            fh = (mp.cos(I) * mp.cos(D), mp.cos(I) * mp.sin(D), mp.sin(I))
+            H = mp.mpf(geom.F_nT) / (4 * mp.pi)
+
+            def dip(x, y, z):
+                r2 = x * x + y * y + z * z
+                s = 3 * (fh[0] * x + fh[1] * y + fh[2] * z) ** 2 - r2 * (fh[0] ** 2 + fh[1] ** 2 + fh[2] ** 2)
+                return s / (r2 * r2 * mp.sqrt(r2))
+
+            for c in cases:
+                ref = H * _gl3_mp(dip, _corners_mp(geom, *c))
+                got = O.entry(geom, *c)
+                assert abs(got - ref) <= 1e-14 * abs(ref), (c, got, ref)
+
+
 # ---------------------------------------------------------------- self cell (P13, R8)
 def test_gravity_self_cell_semi_analytic():
     """Station at the centre of the top face of its cell: the z-integral of z/r^3 is
