@@ -351,8 +351,10 @@ def gravmag_apply(m, op: Operator):
 
 
 def rel_err(x, ref) -> float:
-    x = np.asarray(x, dtype=np.float64).ravel()
-    ref = np.asarray(ref, dtype=np.float64).ravel()
+    """Relative 2-norm error ||x - ref|| / ||ref|| (complex inputs keep their imaginary parts)."""
+    x, ref = np.asarray(x), np.asarray(ref)
+    dt = np.complex128 if (np.iscomplexobj(x) or np.iscomplexobj(ref)) else np.float64
+    x, ref = x.astype(dt).ravel(), ref.astype(dt).ravel()
     return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
 
 

@@ -1,12 +1,14 @@
 """GPU products against the CPU oracle (the parity gate).
 
-FP64 applies must match the long-double dense oracle to a relative 2-norm error
-of 1e-12, FP32 applies to 1e-5 (the paper's measure, Sec. 5).  Double-float
+FP64 applies must match the binary128 dense oracle to a relative 2-norm error
+of 1e-12, FP32 applies to 1e-5 (the paper's measure, Sec. 5), and every element
+must lie within the same fraction of the largest reference element.  Double-float
 (DF64: FP64 vectors, arithmetic on pairs of FP32 values) applies are held to
-the FP64 gate.  Small cases are
-compared element by element over the whole vector; the large workloads at
-sampled stations / cells the oracle computes one by one (stored by
-tests/golden/make_golden.py, which calls only the oracle).
+the FP64 gate.  Small cases are compared over the whole vector; the large
+workloads at 64 sampled stations and 64 sampled cells the oracle computes one
+by one (stored by tests/golden/make_golden.py, which calls only the oracle).
+Two GPU paths in FP64 (codelet and generic kernels, real and complex spectra)
+are held to 1e-13 against each other.
 """
 import json
 import os
@@ -16,7 +18,7 @@ import pytest
 
 import oracle as O
 from paper_1912_06976_gb300 import workloads as W
-from tests.conftest import rel_err
+from tests.conftest import assert_close, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -50,8 +52,8 @@ def test_grav16_full_vs_oracle(gm, prec):
     geom = geometry(w)
     m, d = W.model("grav16"), W.data("grav16")
     fwd, tr = run(gm, w, prec, m, d)
-    assert rel_err(fwd, O.forward(geom, m)) < TOL[prec]
-    assert rel_err(tr, O.transpose(geom, d)) < TOL[prec]
+    assert_close(fwd, O.forward(geom, m), TOL[prec])
+    assert_close(tr, O.transpose(geom, d), TOL[prec])
 
 
 @pytest.mark.parametrize("prec", [1, 0, 2])
@@ -63,8 +65,8 @@ def test_random_small_shapes_vs_oracle(gm, prec, seed):
     m = W.random_vector(w.model_shape, seed)
     d = W.random_vector(w.data_shape, seed + 100)
     fwd, tr = run(gm, w, prec, m, d)
-    assert rel_err(fwd, O.forward(geom, m)) < TOL[prec]
-    assert rel_err(tr, O.transpose(geom, d)) < TOL[prec]
+    assert_close(fwd, O.forward(geom, m), TOL[prec])
+    assert_close(tr, O.transpose(geom, d), TOL[prec])
 
 
 EDGE = [
@@ -86,8 +88,8 @@ def test_edge_shapes_vs_oracle(gm, prec, w):
     m = W.random_vector(w.model_shape, 5)
     d = W.random_vector(w.data_shape, 6)
     fwd, tr = run(gm, w, prec, m, d)
-    assert rel_err(fwd, O.forward(geom, m)) < TOL[prec]
-    assert rel_err(tr, O.transpose(geom, d)) < TOL[prec]
+    assert_close(fwd, O.forward(geom, m), TOL[prec])
+    assert_close(tr, O.transpose(geom, d), TOL[prec])
 
 
 def test_variable_layer_depths_vs_oracle(gm):
@@ -103,8 +105,8 @@ def test_variable_layer_depths_vs_oracle(gm):
         d = W.random_vector((6, 9), 2)
         f = op.forward(torch.as_tensor(m, dtype=dt, device="cuda")).double().cpu().numpy()
         t = op.transpose(torch.as_tensor(d, dtype=dt, device="cuda")).double().cpu().numpy()
-        assert rel_err(f, O.forward(geom, m)) < TOL[prec]
-        assert rel_err(t, O.transpose(geom, d)) < TOL[prec]
+        assert_close(f, O.forward(geom, m), TOL[prec])
+        assert_close(t, O.transpose(geom, d), TOL[prec])
 
 
 def _golden(name):
@@ -120,8 +122,22 @@ def test_full_size_sampled_vs_oracle(gm, name, prec):
     g = _golden(name)
     w = W.WORKLOADS[name]
     fwd, tr = run(gm, w, prec, W.model(name, g["model_seed"]), W.data(name, g["data_seed"]))
-    assert rel_err(fwd.ravel()[g["forward_stations"]], g["forward"]) < TOL[prec]
-    assert rel_err(tr.ravel()[g["transpose_cells"]], g["transpose"]) < TOL[prec]
+    assert_close(fwd.ravel()[g["forward_stations"]], g["forward"], TOL[prec])
+    assert_close(tr.ravel()[g["transpose_cells"]], g["transpose"], TOL[prec])
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_full_size_fp64_error_levels(gm, prec):
+    """The FP64 and double-float products on the 300x250x60 grid against the binary128 oracle
+    samples, well inside the 1e-12 gate: the forward at rounding level (5e-16 FP64, 6e-15
+    double-float measured), the transpose at the level of the FP64 set-up entries' rounding
+    (1.1e-13 measured: a white data vector weights the deep and far entries, whose 4-point
+    corner differences cancel by about (r / cell)^2)."""
+    g = _golden("grav300")
+    w = W.WORKLOADS["grav300"]
+    fwd, tr = run(gm, w, prec, W.model("grav300", g["model_seed"]), W.data("grav300", g["data_seed"]))
+    assert_close(fwd.ravel()[g["forward_stations"]], g["forward"], 2e-14)
+    assert_close(tr.ravel()[g["transpose_cells"]], g["transpose"], 4e-13)
 
 
 @pytest.mark.parametrize("name", ["mag64", "grav300"])
@@ -131,8 +147,8 @@ def test_fp32_whole_vector_vs_fp64(gm, name):
     m, d = W.model(name, 0), W.data(name, 0)
     f64, t64 = run(gm, w, 1, m, d)
     f32, t32 = run(gm, w, 0, m, d)
-    assert rel_err(f32, f64) < 1e-5
-    assert rel_err(t32, t64) < 1e-5
+    assert_close(f32, f64, 1e-5)
+    assert_close(t32, t64, 1e-5)
 
 
 def test_spectrum_is_fft_of_oracle_generator(gm):
@@ -152,7 +168,7 @@ def test_spectrum_is_fft_of_oracle_generator(gm):
                 T[r, v % Ny, u % Nx] = O.entry(geom, i, j, i - u, j - v, r)
     ref = np.fft.rfft2(T)  # [r][ky][kx]
     got = np.transpose(S, (1, 2, 0))
-    assert rel_err(got, ref) < 1e-12
+    assert_close(got, ref, 1e-12)
     op.close()
 
 
@@ -182,7 +198,7 @@ def test_linearity(gm):
     m2 = torch.as_tensor(W.random_vector(w.model_shape, 2), device="cuda")
     lhs = op.forward(2.5 * m1 - 0.5 * m2)
     rhs = 2.5 * op.forward(m1) - 0.5 * op.forward(m2)
-    assert rel_err(lhs.cpu().numpy(), rhs.cpu().numpy()) < 1e-14
+    assert_close(lhs.cpu().numpy(), rhs.cpu().numpy(), 1e-14)
     op.close()
 
 
@@ -230,11 +246,13 @@ def test_codelet_path_matches_generic_path(gm, name, prec, monkeypatch):
     monkeypatch.setenv("GM_GENERIC_FFT", "1")
     ref_f, ref_t = run(gm, w, prec, m, d)
     monkeypatch.delenv("GM_GENERIC_FFT")
+    # the generic kernels take complex spectra: the codelet run does too, so that the two differ
+    # only by the rounding of their FFT orders (measured 4e-16 in FP64 on the 300x250x60 grid)
+    monkeypatch.setenv("GM_COMPLEX_SPECTRA", "1")
     got_f, got_t = run(gm, w, prec, m, d)
-    # FP64: the bound of the oracle gate (the 300x250x60 transpose is 8e-13 from the oracle itself)
-    tol = 1e-12 if prec == 1 else 2e-6
-    assert rel_err(got_f, ref_f) < tol
-    assert rel_err(got_t, ref_t) < tol
+    tol = 1e-13 if prec == 1 else 2e-6
+    assert_close(got_f, ref_f, tol)
+    assert_close(got_t, ref_t, tol)
 
 
 def test_gravity_real_spectra_are_the_fft_of_the_oracle_generator(gm):
@@ -256,7 +274,7 @@ def test_gravity_real_spectra_are_the_fft_of_the_oracle_generator(gm):
             for u in range(-(w.nx - 1), w.sx):
                 i = max(u, 0)
                 T[r, v % Ny, u % Nx] = O.entry(geom, i, j, i - u, j - v, r)
-    assert rel_err(np.transpose(S, (1, 2, 0)), np.fft.rfft2(T)) < 1e-12
+    assert_close(np.transpose(S, (1, 2, 0)), np.fft.rfft2(T), 1e-12)
     op.close()
 
 
@@ -275,10 +293,15 @@ def test_gravity_real_spectra_match_complex_spectra(gm, monkeypatch, name, prec)
     assert op.info.spectrum_real == 1
     op.close()
     got_f, got_t = run(gm, w, prec, m, d)
-    # FP64 / DF64: the bound of the oracle gate (the 300x250x60 transpose is 8e-13 from the oracle itself)
-    tol = 2e-6 if prec == 0 else 1e-12
-    assert rel_err(got_f, ref_f) < tol
-    assert rel_err(got_t, ref_t) < tol
+    # FP64 / DF64: the real even form keeps Re(w conj(T)), i.e. it averages the FP64 entries
+    # k(dx, dy) and k(-dx, dy), which agree exactly in exact arithmetic (the gravity kernel is even,
+    # Sec. 2.2.3) but differ in FP64 by the rounding of the entries' 4-point corner difference,
+    # about (r / cell)^2 eps relative for a cell at distance r: ~1e-13 in the deep layers of the
+    # 300x250x60 grid.  A white data vector sums those errors incoherently in the transpose
+    # (measured 1.3e-13 between the two forms, each ~1.1e-13 from the binary128 oracle).
+    tol = 2e-6 if prec == 0 else 5e-13
+    assert_close(got_f, ref_f, tol)
+    assert_close(got_t, ref_t, tol)
 
 
 def test_asymmetric_padding_and_magnetic_keep_complex_spectra(gm):
@@ -329,8 +352,8 @@ def test_df64_whole_vector_vs_fp64(gm, name):
     m, d = W.model(name, 0), W.data(name, 0)
     f64, t64 = run(gm, w, 1, m, d)
     fdf, tdf = run(gm, w, 2, m, d)
-    assert rel_err(fdf, f64) < 1e-13, rel_err(fdf, f64)
-    assert rel_err(tdf, t64) < 1e-13, rel_err(tdf, t64)
+    assert_close(fdf, f64, 1e-13)
+    assert_close(tdf, t64, 1e-13)
 
 
 @pytest.mark.parametrize("name", ["grav16", "mag64"])

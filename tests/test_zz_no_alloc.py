@@ -7,22 +7,30 @@ synchronisation an allocation may cause, and services that must not grow their
 device footprint after start-up.  Its scratch is a fixed array inside the
 library, shared by all calls, so these tests check that two calls in a row --
 the second one seeing the first one's leftovers -- each give the same result
-as gm_cgls, and that a grid too large for the array is refused with a clear
-error.  This file is collected last so that a stop-at-first-failure run has
+as gm_cgls in every precision (FP32, FP64 and double-float, whose vectors are
+FP64), that the device's free memory is the same before and after each call,
+and that a grid too large for the array is refused with a clear error.  This file is collected last so that a stop-at-first-failure run has
 already run every other test.
 """
 import numpy as np
 import pytest
 
 from paper_1912_06976_gb300 import workloads as W
-from tests.conftest import rel_err
+from tests.conftest import assert_close, rel_err
 
 pytestmark = pytest.mark.gpu
 
-TOL = {1: 1e-12, 0: 1e-5}
+TOL = {1: 1e-12, 0: 1e-5, 2: 1e-12}
 
 
-@pytest.mark.parametrize("prec", [1, 0])
+def _free_bytes():
+    import torch
+
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0]
+
+
+@pytest.mark.parametrize("prec", [1, 0, 2])
 def test_noalloc_cgls_matches_cgls_twice_in_a_row(gm, prec):
     import torch
 
@@ -35,9 +43,11 @@ def test_noalloc_cgls_matches_cgls_twice_in_a_row(gm, prec):
         x0 = torch.as_tensor(x0_np, dtype=dt, device="cuda") if x0_np is not None else None
         ref, ref_res = op.cgls(d, alpha, iters, x0=x0)
         out = torch.empty(op.model_shape, dtype=dt, device="cuda")
+        free0 = _free_bytes()
         got, got_res = op.cgls_noalloc(d, alpha, iters, out, x0=x0)
+        assert _free_bytes() == free0  # the call allocated no device memory
         assert got.data_ptr() == out.data_ptr()
-        assert rel_err(got.double().cpu().numpy(), ref.double().cpu().numpy()) < TOL[prec]
+        assert_close(got.double().cpu().numpy(), ref.double().cpu().numpy(), TOL[prec])
         np.testing.assert_allclose(got_res, ref_res, rtol=TOL[prec])
     op.close()
 
