@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
     const size_t lsz = (size_t)p.LD * p.LH * p.LW;  // stored (not up-sampled) x per channel
     const uint32_t idesc = gm::tc::instr_desc_bf16(128, bn);
     bool ok = true;
+    int committed = -1;  // last K block whose MMAs were committed (the same in every thread)
 
     for (int it = 0; it < nkb; ++it) {
         const int kb = kb0 + it;
@@ -310,6 +311,7 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
                                  it > 0 || j > 0);
             gm::tc::commit(&bars[s]);
         }
+        committed = it;
     }
     if (ok) {
         const bool got = gm::tc::mbar_wait(&bars[(nkb - 1) & 1], ((nkb - 1) >> 1) & 1, p.wait_limit);
@@ -317,6 +319,14 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
     }
     if (!ok) {
         if (t == 0) atomicExch(err, 1);
+        // A wait gave up while MMAs may still be reading the shared-memory stages and writing this
+        // block's tensor memory.  The last commit arrives only once every MMA the block issued is
+        // done (a commit tracks all earlier tcgen05 operations of its thread), so wait for it once
+        // more, again bounded, before the block frees its columns and exits.  If that wait gives up
+        // too, the columns are freed anyway: holding them would stall the next allocation on this
+        // SM without limit, and the launch has already reported the error, so its outputs are void.
+        if (committed >= 0) (void)gm::tc::mbar_wait(&bars[committed & 1], (committed >> 1) & 1, p.wait_limit);
+        __syncthreads();
     } else {
         gm::tc::fence_after_sync();
         const int warp = t >> 5;
