@@ -13,7 +13,7 @@ N > 1 (launched by torch.distributed.run): every rank runs an independent
 replica on its own GPU (the operator has no exchange step on one GPU's data);
 value = applies of all ranks / the slowest rank's time ("replicas only").
 
---impl reference times the CPU oracle (dense long-double prism entries, direct
+--impl reference times the CPU oracle (dense binary128 prism entries, direct
 summation) on bounded samples of the same workload on the host's cores.
 """
 from __future__ import annotations
@@ -203,7 +203,7 @@ def cpu_oracle_sample(w, budget_s: float = 12.0, min_batches: int = 1, per_threa
         batches += 1
     apply_s = t_total / done * w.m * w.n
     return {"value": 1.0 / apply_s, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{done} uniformly sampled entries of G ({t_total:.1f} s, long double), scaled to the "
+            "sample": f"{done} uniformly sampled entries of G ({t_total:.1f} s, binary128), scaled to the "
                       f"m*n = {w.m * w.n} entries one forward or transpose product evaluates",
             "seconds": t_total}
 
@@ -219,6 +219,93 @@ def cpu_oracle_one_core(w, budget_s: float = 3.0):
     finally:
         O.set_threads(n)
     return {"value_1core": r["value"], "sample_1core": r["sample"]}
+
+
+def host_cpu():
+    """Model name and logical CPU count of the host (lscpu where present)."""
+    import platform
+
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count() or 1,
+            "machine": platform.machine()}
+
+
+def cpu_fft_baseline(gm, w, budget_s: float = 3.0):
+    """The host-CPU FFT baseline on the benchmark workload: the GPU path's algorithm with scipy.fft
+    on all host cores (batched R2C over the layers, depth multiply-accumulate, one inverse for G m;
+    one forward and n_z inverses for G^T d), on the library's own spectra, FP32 and FP64.  Set-up
+    and FFT planning are excluded (Sec. 5); a warm-up apply, then repetitions for about budget_s."""
+    import numpy as np
+
+    from paper_1912_06976_gb300 import workloads as W
+
+    workers = os.cpu_count() or 1
+    m_np, d_np = W.model(w.name, 0), W.data(w.name, 0)
+    out = {"cores": workers, "host": host_cpu(), "library": "scipy.fft (pocketfft) rfft2 / irfft2",
+           "algorithm": "same as the GPU path, on the library's spectra"}
+    for prec, npdt, name in ((gm.F32, np.float32, "fp32"), (gm.F64, np.float64, "fp64")):
+        op = gm.Operator.from_workload(w, precision=prec)
+        spec = op.spectrum()
+        op.close()
+        mm, dd = m_np.astype(npdt), d_np.astype(npdt)
+        cpu_fft_apply(spec, w.nz, w.ny, w.nx, w.sy, w.sx, mm, dd, workers)
+        times = []
+        t_end = time.perf_counter() + budget_s
+        while len(times) < 3 or time.perf_counter() < t_end:
+            t0 = time.perf_counter()
+            cpu_fft_apply(spec, w.nz, w.ny, w.nx, w.sy, w.sx, mm, dd, workers)
+            times.append(time.perf_counter() - t0)
+        out[name] = {"value": 2.0 / statistics.mean(times), "unit": UNIT, "reps": len(times),
+                     "ms_per_step_mean": 1e3 * statistics.mean(times),
+                     "ms_per_step_median": 1e3 * statistics.median(times)}
+        del spec
+    return out
+
+
+def oracle_dense_timings(names=("grav16", "mag64"), budget_s: float = 2.0):
+    """The dense oracle (every entry of a row of G from its prism formula, direct sum) on the two
+    small workloads, at one host thread and at all of them: rows of d = G m per second, scaled to
+    one forward product (m rows).  A bounded sample of stations per measurement."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1912_06976_gb300 import workloads as W
+
+    nthreads = O.threads()
+    res = {"host": host_cpu(), "arithmetic": f"binary128 ({O.significand_bits()}-bit significand)"}
+    for name in names:
+        w = W.WORKLOADS[name]
+        geom = O.Geometry(w.sx, w.sy, w.nz, w.dx, w.dy, w.zplanes, w.pxl, w.pxr, w.pyl, w.pyr, w.kind,
+                          w.incl_deg, w.decl_deg, w.F_nT)
+        m = W.model(name, 0)
+        row = {"stations": w.m, "cells": w.n}
+        for label, th in (("1core", 1), ("all_cores", nthreads)):
+            O.set_threads(th)
+            try:
+                rng = np.random.default_rng(7)
+                rows, t = 0, 0.0
+                while t < budget_s and rows < w.m:
+                    k = min(w.m - rows, th)
+                    st = rng.choice(w.m, size=k, replace=False)
+                    t0 = time.perf_counter()
+                    O.forward(geom, m, stations=st)
+                    t += time.perf_counter() - t0
+                    rows += k
+            finally:
+                O.set_threads(nthreads)
+            per_product = t / rows * w.m
+            row[label] = {"applies_per_s": 1.0 / per_product, "threads": th, "rows_timed": rows,
+                          "seconds": t}
+        res[name] = row
+    return res
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -240,11 +327,11 @@ def run_reference(args):
     value = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / max(args.steps, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f80/f128 (long double)",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f128 (binary128)",
             "data": "synthetic", "config": workload_config(w),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                              "sample": f"each step: {per_thread * r['cores']} uniformly sampled entries of G "
-                                       f"({per_thread} per thread, long double), scaled to the m*n entries of one "
+                                       f"({per_thread} per thread, binary128), scaled to the m*n entries of one "
                                        f"product"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -499,6 +586,9 @@ def run_ours(args):
         cpu = cpu_oracle_sample(w)
         cpu.pop("seconds", None)
         cpu.update(cpu_oracle_one_core(w))
+        cpu["host"] = host_cpu()
+        extra["cpu_fft"] = cpu_fft_baseline(gm, w)
+        extra["oracle_dense"] = oracle_dense_timings()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps,
