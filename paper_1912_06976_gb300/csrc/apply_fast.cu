@@ -97,7 +97,8 @@ void choose_groups(const gm_plan *p, bool tr, int *groups, int *lpg) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const YOps<R> *yo = y_ops<R>(g.NPy);
     const int cols = yo ? (tr ? yo->cols_tr : yo->cols) : 1;
-    const void *k = yo ? (tr ? yo->kern_tr : yo->kern_fwd) : nullptr;
+    const int real = p->spec_real ? 1 : 0;
+    const void *k = yo ? (tr ? yo->kern_tr[real] : yo->kern_fwd[real]) : nullptr;
     const size_t sm = yo ? (tr ? yo->smem_tr : yo->smem_fwd) : 0;
     if (k) {
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

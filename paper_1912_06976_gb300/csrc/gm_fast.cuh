@@ -244,6 +244,52 @@ __device__ __forceinline__ void load_table(C *dst, const C *__restrict__ src) {
     }
 }
 
+// Per-pass twiddle layout for the pass-2 items of a transform with radices (P1, P2):
+// dst[rr * P1 + j] = exp(-2 pi i rr j / N) for rr < P2, j < P1 (N = P1 P2), copied from the N-entry
+// table.  Consecutive items j then read consecutive entries (no shared-memory bank conflicts,
+// unlike tw[rr * j], whose stride rr sends even rr to a few banks).
+template <int P1, int P2, int THREADS, typename C>
+__device__ __forceinline__ void load_pass_table(C *dst, const C *__restrict__ src) {
+    constexpr int N = P1 * P2, B = (N + THREADS - 1) / THREADS;
+    C tmp[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int i = threadIdx.x + b * THREADS;
+        if (i < N) {
+            const int rr = i / P1, j = i - rr * P1;
+            tmp[b] = ld_nc(src + rr * j);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int i = threadIdx.x + b * THREADS;
+        if (i < N) dst[i] = tmp[b];
+    }
+}
+
+// pass-2 twiddles of item j from a per-pass table (conjugated for the inverse)
+template <int P1, int P2, bool INV, typename C>
+__device__ __forceinline__ void pass2_twiddle_pass_table(C (&v)[P2], const C *tp, int j) {
+#pragma unroll
+    for (int rr = 1; rr < P2; ++rr) {
+        C w = tp[rr * P1 + j];
+        if (INV) w = c_conj(w);
+        v[rr] = c_mul(v[rr], w);
+    }
+}
+
+// The column kernels keep the per-pass twiddle tables in FP32 only: the FP64 and double-float
+// kernels are bound by the FP64 pipe or by shared memory (the tables would push the 768-point
+// FP64 transpose kernel past the 227 KB a block may use), so they index the N-entry table.
+template <typename C> constexpr bool pass_tables() { return sizeof(C) == 8; }
+
+// Blocks per SM the column kernels are compiled for: two for FP32 when two blocks' shared memory
+// fits an SM (the register limit this sets, 128 per thread, holds the kernels without spills),
+// else one (FP64 and double-float column kernels are limited to one block by shared memory).
+template <typename C> constexpr int col_min_blocks(size_t smem_bytes) {
+    return (sizeof(C) == 8 && smem_bytes <= 110 * 1024) ? 2 : 1;
+}
+
 // ------------------------------------------------------------------------------------------
 // Real rows -> half spectra (two rows per complex transform, N = R1*R2 = N'_x).
 // Block (pair group, layer) transforms rows q0 .. q0 + 2*PAIRS - 1 of `layer` of
@@ -454,17 +500,26 @@ __device__ __forceinline__ void cols_sum_inverse(const C *__restrict__ part, int
 // Pass-2 thread (c, j) owns k = j + R1*s (s < R2) for every layer, so acc stays in registers.
 // The last block of a column group to finish (counted with an atomic; nothing waits) sums the
 // groups' partials in group order and runs the inverse column transform into B[kx][0:sy].
-template <typename C, int R1, int R2, int COLS, int LSTEP, int THREADS>
-__global__ void __launch_bounds__(THREADS)
+// SPEC selects the spectrum form: 0 complex, 1 real even (gravity, equal padding), fixed at
+// compile time so that each variant carries only its own multiply-accumulate (the unused one
+// would otherwise shape the register allocation and schedule: 13 % of the FP32 kernel's time on
+// the 672 x 560 grid), or 2: chosen at run time by spec_real (one kernel for both, used by the
+// FP64 and double-float builds to keep their compile time down).
+// Shared memory: tw [N] | tw2 [R2][R1] (per-pass layout, FP32) | exchanges.
+template <typename C, int R1, int R2, int COLS, int LSTEP, int THREADS, int SPEC, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
     k_cols_fwd_mac(const C *__restrict__ A, const C *__restrict__ S, C *__restrict__ part, C *__restrict__ B,
                    unsigned int *__restrict__ counters, int Kx, int nz, int ny, int nyp, int sy,
                    int layers_per_group, int ngroups, const C *__restrict__ twg, int spec_real, int pxl, int pyl,
                    const C *__restrict__ twx) {
+    const bool REAL = SPEC == 2 ? spec_real != 0 : SPEC == 1;
     constexpr int N = R1 * R2, EX = Ex<R1, R2>::value;
     static_assert(COLS * R1 <= THREADS, "one pass-2 owner per thread");
     extern __shared__ unsigned char smem_raw[];
+    constexpr bool PT = pass_tables<C>();
     C *tw = reinterpret_cast<C *>(smem_raw);  // [N]
-    C *ex = tw + N;                           // [COLS*LSTEP][EX]
+    C *tw2 = tw + N;                          // [R2][R1] (PT)
+    C *ex = tw2 + (PT ? N : 0);               // [COLS*LSTEP][EX]
     __shared__ unsigned int s_last;
     const int kx0 = blockIdx.x * COLS;
     const int g = blockIdx.y;
@@ -479,6 +534,7 @@ __global__ void __launch_bounds__(THREADS)
     for (int s = 0; s < R2; ++s) acc[s] = c_make<C>(0, 0);
     const uint64_t pol_s = policy_evict_first();
     load_table<N, THREADS>(tw, twg);
+    if (PT) load_pass_table<R1, R2, THREADS>(tw2, twg);
     const int row_lines = (ny * (int)sizeof(C) + 127) / 128;  // lines of one A column (pitch nyp: whole lines)
     pdl_wait();
     for (int r = r_begin; r < r_end; r += LSTEP) {
@@ -512,9 +568,12 @@ __global__ void __launch_bounds__(THREADS)
                 if (rl < r_end) {
                     C v[R2];
                     pass2_gather<R1, R2>(v, ex + (oc * LSTEP + l) * EX, oj);
-                    pass2_twiddle_table<R1, R2, false>(v, tw, oj);
+                    if (PT)
+                        pass2_twiddle_pass_table<R1, R2, false>(v, tw2, oj);
+                    else
+                        pass2_twiddle_table<R1, R2, false>(v, tw, oj);
                     cl::Dft<R2, false>::run(v);
-                    if (spec_real) {
+                    if (REAL) {
                         using Rr = typename real_of<C>::type;
                         const Rr *Er = reinterpret_cast<const Rr *>(S) + ((size_t)okx * nz + rl) * (N / 2 + 1);
 #pragma unroll
@@ -535,7 +594,7 @@ __global__ void __launch_bounds__(THREADS)
     }
     pdl_trigger();
     if (owner && okx < Kx) {
-        if (spec_real)  // the phase of the embedded generator, once for the whole depth sum
+        if (REAL)  // the phase of the embedded generator, once for the whole depth sum
             apply_phase<R1, R2, false>(acc, twx, 2 * (Kx - 1), pxl, okx, tw, N, pyl, oj);
         C *o = part + ((size_t)g * Kx + okx) * N + oj;
 #pragma unroll
@@ -561,19 +620,25 @@ __global__ void __launch_bounds__(THREADS)
 // Dh = FFT_y(D1[kx][0:sy]) once (radices (R1, R2)); its pass-2 owners (c, j) keep
 // Dh[j + R1*s] in registers; then for each layer the inverse transform (radices (R2, R1))
 // of conj(S[kx][r]) * Dh starts from exactly those values, and A2[kx][r][q] = result[q], q < ny.
-template <typename C, int R1, int R2, int COLS, int LSTEP, int THREADS>
-__global__ void __launch_bounds__(THREADS)
+// SPEC as in k_cols_fwd_mac.  Shared memory: tw [N] | twf [R2][R1] (forward pass 2) | twi [R1][R2]
+// (inverse pass 2; both FP32 only) | exchanges.
+template <typename C, int R1, int R2, int COLS, int LSTEP, int THREADS, int SPEC, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
     k_cols_tr(const C *__restrict__ D1, const C *__restrict__ S, C *__restrict__ A2, int Kx, int nz, int ny, int nyp,
               int sy, int layers_per_group, const C *__restrict__ twg, int spec_real, int pxl, int pyl,
               const C *__restrict__ twx) {
+    const bool REAL = SPEC == 2 ? spec_real != 0 : SPEC == 1;
     constexpr int N = R1 * R2;
     constexpr int EXF = Ex<R1, R2>::value;  // forward exchange (pass-1 radix R1)
     constexpr int EXI = Ex<R2, R1>::value;  // inverse exchange (pass-1 radix R2)
     constexpr int EXM = EXF > EXI ? EXF : EXI;
     static_assert(COLS * R1 <= THREADS, "one owner per thread");
     extern __shared__ unsigned char smem_raw[];
+    constexpr bool PT = pass_tables<C>();
     C *tw = reinterpret_cast<C *>(smem_raw);  // [N]
-    C *ex = tw + N;                           // [COLS*LSTEP][EXM]
+    C *twf = tw + N;                          // [R2][R1] (PT)
+    C *twi = twf + (PT ? N : 0);              // [R1][R2] (PT)
+    C *ex = twi + (PT ? N : 0);               // [COLS*LSTEP][EXM]
     const int kx0 = blockIdx.x * COLS;
     const int g = blockIdx.y;
     const int r_begin = g * layers_per_group;
@@ -586,10 +651,14 @@ __global__ void __launch_bounds__(THREADS)
     if (t < COLS * LSTEP) {
         const int c = t / LSTEP, l = t - c * LSTEP;
         const int kx = kx0 + c, rn = r_begin + l;
-        if (kx < Kx && rn < r_end && !spec_real)
+        if (kx < Kx && rn < r_end && !REAL)
             prefetch_l2(S + ((size_t)kx * nz + rn) * N, (unsigned int)(sizeof(C) * N));
     }
     load_table<N, THREADS>(tw, twg);
+    if (PT) {
+        load_pass_table<R1, R2, THREADS>(twf, twg);
+        load_pass_table<R2, R1, THREADS>(twi, twg);
+    }
     pdl_wait();
     // forward transform of the data columns: pass 1 items j < R2 take D1[kx][j + R2*rr]
     for (int it = t; it < COLS * R2; it += THREADS) {
@@ -608,9 +677,12 @@ __global__ void __launch_bounds__(THREADS)
     C dh[R2];
     if (owner) {
         pass2_gather<R1, R2>(dh, ex + oc * EXM, oj);
-        pass2_twiddle_table<R1, R2, false>(dh, tw, oj);
+        if (PT)
+            pass2_twiddle_pass_table<R1, R2, false>(dh, twf, oj);
+        else
+            pass2_twiddle_table<R1, R2, false>(dh, tw, oj);
         cl::Dft<R2, false>::run(dh);
-        if (spec_real && okx < Kx)  // conj(T_r) Dh = E_r (conj(w) Dh): conj(w) once for all layers
+        if (REAL && okx < Kx)  // conj(T_r) Dh = E_r (conj(w) Dh): conj(w) once for all layers
             apply_phase<R1, R2, true>(dh, twx, 2 * (Kx - 1), pxl, okx, tw, N, pyl, oj);
     }
     __syncthreads();
@@ -618,7 +690,7 @@ __global__ void __launch_bounds__(THREADS)
         if (t < COLS * LSTEP) {
             const int c = t / LSTEP, l = t - c * LSTEP;
             const int kx = kx0 + c, rn = r + LSTEP + l;
-            if (kx < Kx && rn < r_end && !spec_real)
+            if (kx < Kx && rn < r_end && !REAL)
                 prefetch_l2(S + ((size_t)kx * nz + rn) * N, (unsigned int)(sizeof(C) * N));
         }
         // inverse pass 1 (radix R2) by the owners: y[oj + R1*rr] = conj(S) * Dh, rr < R2
@@ -628,7 +700,7 @@ __global__ void __launch_bounds__(THREADS)
                 const int rl = r + l;
                 if (rl < r_end) {
                     C v[R2];
-                    if (spec_real) {
+                    if (REAL) {
                         using Rr = typename real_of<C>::type;
                         const Rr *Er = reinterpret_cast<const Rr *>(S) + ((size_t)okx * nz + rl) * (N / 2 + 1);
 #pragma unroll
@@ -655,7 +727,10 @@ __global__ void __launch_bounds__(THREADS)
             if (kx >= Kx || rl >= r_end) continue;
             C v[R1];
             pass2_gather<R2, R1>(v, ex + (c * LSTEP + l) * EXM, j);
-            pass2_twiddle_table<R2, R1, true>(v, tw, j);
+            if (PT)
+                pass2_twiddle_pass_table<R2, R1, true>(v, twi, j);
+            else
+                pass2_twiddle_table<R2, R1, true>(v, tw, j);
             cl::Dft<R1, true>::run(v);
             C *o = A2 + ((size_t)kx * nz + rl) * nyp;
 #pragma unroll

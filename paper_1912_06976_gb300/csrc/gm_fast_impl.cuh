@@ -96,25 +96,42 @@ template <typename R, int Y1, int Y2> struct ColCfg {
     static constexpr int T_TR = cols_threads<Y1>();
 };
 
+// shared memory of the column kernels: the N-entry twiddle table, the per-pass tables (one for the
+// forward kernel, two for the transpose kernel) and the exchanges
 template <typename R, int Y1, int Y2>
-size_t fwd_mac_smem(int) {
-    return sizeof(cpx_t<R>) * (Y1 * Y2 + cols_per_cta<Y1>() * kLstep * fast::Ex<Y1, Y2>::value);
+constexpr size_t fwd_mac_smem_c() {
+    constexpr int tables = fast::pass_tables<cpx_t<R>>() ? 2 : 1;
+    return sizeof(cpx_t<R>) * (tables * Y1 * Y2 + cols_per_cta<Y1>() * kLstep * fast::Ex<Y1, Y2>::value);
 }
 template <typename R, int Y1, int Y2>
-size_t tr_smem() {
+constexpr size_t tr_smem_c() {
     constexpr int a = fast::Ex<Y1, Y2>::value, b = fast::Ex<Y2, Y1>::value;
-    return sizeof(cpx_t<R>) * (Y1 * Y2 + cols_per_cta<Y1>() * kLstep * (a > b ? a : b));
+    constexpr int tables = fast::pass_tables<cpx_t<R>>() ? 3 : 1;
+    return sizeof(cpx_t<R>) * (tables * Y1 * Y2 + cols_per_cta<Y1>() * kLstep * (a > b ? a : b));
 }
-
 template <typename R, int Y1, int Y2>
+size_t fwd_mac_smem(int) { return fwd_mac_smem_c<R, Y1, Y2>(); }
+template <typename R, int Y1, int Y2>
+size_t tr_smem() { return tr_smem_c<R, Y1, Y2>(); }
+
+// The spectrum form of a column kernel: fixed at compile time for FP32 (one kernel per form), chosen
+// at run time for FP64 and double-float (one kernel for both forms, half the compile time).
+template <typename R> constexpr int spec_mode(bool real) {
+    return std::is_same<R, float>::value ? (real ? 1 : 0) : 2;
+}
+template <typename R, int Y1, int Y2, bool REAL>
 const void *fwd_kernel() {
     using CC = ColCfg<R, Y1, Y2>;
-    return (const void *)fast::k_cols_fwd_mac<cpx_t<R>, Y1, Y2, CC::COLS, kLstep, CC::T_FWD>;
+    using C = cpx_t<R>;
+    return (const void *)fast::k_cols_fwd_mac<C, Y1, Y2, CC::COLS, kLstep, CC::T_FWD, spec_mode<R>(REAL),
+                                              fast::col_min_blocks<C>(fwd_mac_smem_c<R, Y1, Y2>())>;
 }
-template <typename R, int Y1, int Y2>
+template <typename R, int Y1, int Y2, bool REAL>
 const void *tr_kernel() {
     using CC = ColCfg<R, Y1, Y2>;
-    return (const void *)fast::k_cols_tr<cpx_t<R>, Y1, Y2, CC::COLS_TR, kLstep, CC::T_TR>;
+    using C = cpx_t<R>;
+    return (const void *)fast::k_cols_tr<C, Y1, Y2, CC::COLS_TR, kLstep, CC::T_TR, spec_mode<R>(REAL),
+                                         fast::col_min_blocks<C>(tr_smem_c<R, Y1, Y2>())>;
 }
 
 template <typename R, int Y1, int Y2>
@@ -127,7 +144,7 @@ cudaError_t cols_fwd_mac(const gm_plan *p, const cpx_t<R> *A, const cpx_t<R> *S,
     const size_t sm = fwd_mac_smem<R, Y1, Y2>(g.nyp);
     auto k = reinterpret_cast<void (*)(const C *, const C *, C *, C *, unsigned int *, int, int, int, int, int, int,
                                        int, const C *, int, int, int, const C *)>(
-        const_cast<void *>(fwd_kernel<R, Y1, Y2>()));
+        const_cast<void *>(p->spec_real ? fwd_kernel<R, Y1, Y2, true>() : fwd_kernel<R, Y1, Y2, false>()));
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
     dim3 grd((g.Kx + COLS - 1) / COLS, p->fast_groups_fwd);
@@ -146,7 +163,8 @@ cudaError_t cols_tr(const gm_plan *p, const cpx_t<R> *D1, const cpx_t<R> *S, cpx
     const Geo &g = p->geo;
     const size_t sm = tr_smem<R, Y1, Y2>();
     auto k = reinterpret_cast<void (*)(const C *, const C *, C *, int, int, int, int, int, int, const C *, int, int,
-                                       int, const C *)>(const_cast<void *>(tr_kernel<R, Y1, Y2>()));
+                                       int, const C *)>(
+        const_cast<void *>(p->spec_real ? tr_kernel<R, Y1, Y2, true>() : tr_kernel<R, Y1, Y2, false>()));
     cudaError_t e = allow_smem(k, sm);
     if (e != cudaSuccess) return e;
     dim3 grd((g.Kx + COLS - 1) / COLS, p->fast_groups_tr);
@@ -177,8 +195,10 @@ YOps<R> make_yops() {
     o.block_tr = CC::T_TR;
     o.smem_fwd = fwd_mac_smem<R, Y1, Y2>(0);
     o.smem_tr = tr_smem<R, Y1, Y2>();
-    o.kern_fwd = fwd_kernel<R, Y1, Y2>();
-    o.kern_tr = tr_kernel<R, Y1, Y2>();
+    o.kern_fwd[0] = fwd_kernel<R, Y1, Y2, false>();
+    o.kern_fwd[1] = fwd_kernel<R, Y1, Y2, true>();
+    o.kern_tr[0] = tr_kernel<R, Y1, Y2, false>();
+    o.kern_tr[1] = tr_kernel<R, Y1, Y2, true>();
     return o;
 }
 

@@ -40,7 +40,7 @@ template <typename R> struct YOps {
     cudaError_t (*tr)(const gm_plan *p, const cpx_t<R> *D1, const cpx_t<R> *S, cpx_t<R> *A2, cudaStream_t s);
     int cols, cols_tr, block_fwd, block_tr;
     size_t smem_fwd, smem_tr;
-    const void *kern_fwd, *kern_tr;
+    const void *kern_fwd[2], *kern_tr[2];  // [0] complex spectra, [1] real even spectra
 };
 
 // nullptr when the length is not on the ladder (defined in fast_x_*.cu, fast_y_*.cu)
