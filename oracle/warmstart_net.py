@@ -21,11 +21,12 @@ convolved axis) and a bias.  Parameters are one flat vector: per layer, in
 the order above, w[co][ci][kd][kh][kw] then b[co].  The library convolves with
 BF16 weights; ``bf16_round`` gives the same weights here (round to nearest
 even of the FP32 value to 8 mantissa bits) so both sides use one set of
-numbers.  Gradients are torch.autograd in float64.  The library's tensor-core kernels also
-round the activations and gradients they multiply to BF16 (summing in FP32); with
-``bf16_operands=True`` the oracle rounds the same operands at the same places (its explicit
-backward formulas are pinned against autograd with the rounding switched off) and sums
-exactly, so only accumulation order and rare rounding-boundary cases differ.
+numbers.  Gradients are torch.autograd in float64.  The library's tensor-core kernels carry
+the FP32 activations and gradients they multiply as two BF16 terms (hi + lo, relative error of
+order 1e-6) and sum in FP32, which the default (exact operand) mode here models.  With
+``bf16_operands=True`` the oracle instead rounds every convolution operand to a single BF16
+value at the places a single-term BF16 GEMM would (its explicit backward formulas are pinned
+against autograd with the rounding switched off).
 
 Pins (tests/test_warmstart_oracle_pins.py): the convolution step against a
 brute-force loop sum, the up-sampling and reshape against index formulas, the
@@ -119,21 +120,27 @@ class _Bf16OperandConv(torch.autograd.Function):
         return dx, dw, gr.sum(dim=(0, 2, 3, 4)), None, None, None
 
 
-def conv_bf16(mode, w, x=None, g=None, b=None, stride=1, in_shape=None):
-    """One convolution with BF16-rounded operands summed exactly (the three products of
-    ``_Bf16OperandConv``): mode 0 conv(bf16(x), bf16(w)) + b; mode 1 the data gradient of shape
-    in_shape from bf16(g); mode 2 (weight gradient from bf16(x), bf16(g), sum of bf16(g))."""
+def conv_bf16(mode, w, x=None, g=None, b=None, stride=1, in_shape=None, round_operands=True):
+    """One convolution with BF16 weights, summed exactly (the three products of
+    ``_Bf16OperandConv``): mode 0 conv(x, bf16(w)) + b; mode 1 the data gradient of shape
+    in_shape from g; mode 2 (weight gradient from x and g, sum of g).  With round_operands the
+    operands x and g are rounded to BF16 too; without, they enter as the given FP32 values."""
     wt = torch.as_tensor(bf16_round(np.asarray(w, dtype=np.float32)).reshape(np.shape(w)))
     kd = wt.shape[2]
     st, pad = (1, stride, stride), (kd // 2, 1, 1)
+
+    def operand(a):
+        a = np.asarray(a, dtype=np.float32)
+        return torch.as_tensor((bf16_round(a) if round_operands else a.astype(np.float64)).reshape(np.shape(a)))
+
     if mode == 0:
-        xr = torch.as_tensor(bf16_round(np.asarray(x, dtype=np.float32)).reshape(np.shape(x)))
+        xr = operand(x)
         bt = None if b is None else torch.as_tensor(np.asarray(b, dtype=np.float64))
         return F.conv3d(xr, wt, bt, stride=st, padding=pad).numpy()
-    gr = torch.as_tensor(bf16_round(np.asarray(g, dtype=np.float32)).reshape(np.shape(g)))
+    gr = operand(g)
     if mode == 1:
         return torch.nn.grad.conv3d_input(tuple(in_shape), wt, gr, stride=st, padding=pad).numpy()
-    xr = torch.as_tensor(bf16_round(np.asarray(x, dtype=np.float32)).reshape(np.shape(x)))
+    xr = operand(x)
     dw = torch.nn.grad.conv3d_weight(xr, tuple(wt.shape), gr, stride=st, padding=pad)
     return dw.numpy(), gr.sum(dim=(0, 2, 3, 4)).numpy()
 
@@ -146,12 +153,13 @@ def upsample(x, f):
     return x
 
 
-def f_scaled(layers, d, in_scale, bf16_operands=False, explicit_backward=False):
+def f_scaled(layers, d, in_scale, bf16_operands=False, explicit_backward=False, pre_acts=None):
     """f(in_scale d) for d of shape (N, S, S); returns (N, 16, S, S).
 
-    bf16_operands: every convolution multiplies BF16-rounded operands (see _Bf16OperandConv),
-    as the tensor-core kernels do; explicit_backward without it runs the same explicit
-    gradient formulas with no rounding (used to pin them against autograd)."""
+    bf16_operands: every convolution multiplies BF16-rounded operands (see _Bf16OperandConv);
+    explicit_backward without it runs the same explicit gradient formulas with no rounding
+    (used to pin them against autograd).  pre_acts, if a list, receives the input of every
+    ReLU."""
     x = (in_scale * d).unsqueeze(1).unsqueeze(1)  # N x 1 x 1 x S x S
     for idx, ((ci, co, kd, st, up, relu), (w, b)) in enumerate(zip(LAYERS, layers)):
         if idx == 5:  # the encoder's 512 x 1 x s x s output read as 128 x 4 x s x s
@@ -163,8 +171,21 @@ def f_scaled(layers, d, in_scale, bf16_operands=False, explicit_backward=False):
         else:
             x = F.conv3d(x, w, b, stride=(1, st, st), padding=(kd // 2, 1, 1))
         if relu:
+            if pre_acts is not None:
+                pre_acts.append(x.detach())
             x = torch.relu(x)
     return x[:, 0]
+
+
+def relu_margin(params, d, in_scale=1.0) -> float:
+    """The smallest |input| of any ReLU of f(in_scale d), relative to the rms of its layer's
+    inputs.  The gradient of the network jumps where a ReLU input crosses zero, so two
+    evaluations that differ by a relative e per value agree to e only when this margin is well
+    above e."""
+    pre = []
+    with torch.no_grad():
+        f_scaled(unpack(params), torch.as_tensor(np.asarray(d, dtype=np.float64)), in_scale, pre_acts=pre)
+    return min(float(x.abs().min() / torch.sqrt((x * x).mean())) for x in pre)
 
 
 def forward(params, d, in_scale=1.0, out_scale=1.0, bf16_operands=False) -> np.ndarray:

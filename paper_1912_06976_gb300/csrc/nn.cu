@@ -11,9 +11,12 @@
 //   output   1 x 16 x S x S
 // Weights: FP32 master copies updated by Adam, packed after every update into two BF16 GEMM
 // layouts.  Every convolution (forward, data gradient, weight gradient) is an implicit GEMM on
-// the tensor cores (tcgen05.mma, BF16 operands gathered on the fly from the FP32 activations and
-// gradients, FP32 accumulators in tensor memory); the element-wise steps (scaling, up-sampling,
-// ReLU masks, loss, Adam) are plain CUDA-core kernels.
+// the tensor cores (tcgen05.mma with FP32 accumulators in tensor memory).  The weights enter as
+// BF16; the FP32 activations and gradients are gathered on the fly as two BF16 terms, v = hi + lo
+// with hi = bf16(v) and lo = bf16(v - hi) (relative error below 2^-17, against 2^-9 for hi
+// alone), and each product is accumulated from the terms: x w = hi w + lo w, and for the weight
+// gradient x g = xhi ghi + xhi glo + xlo ghi (the lo lo term is below 2^-18 of the product).
+// The element-wise steps (scaling, up-sampling, ReLU masks, loss, Adam) are plain CUDA-core kernels.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -44,8 +47,9 @@ __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162f
 // Convolutions as implicit GEMMs on the tensor cores (tcgen05, BF16 operands, FP32 accumulators
 // in tensor memory).  One CTA of 256 threads computes a 128 x BN tile of D = A B^T over K in
 // blocks of 64, two shared-memory stages deep: all threads gather the next block of A and B
-// (FP32 activations / gradients rounded to BF16, packed BF16 weights) while the tensor cores
-// multiply the previous one; thread 0 issues the MMAs and commits each stage to an mbarrier.
+// (FP32 activations / gradients as BF16 hi and lo terms, packed BF16 weights) while the tensor
+// cores multiply the previous one; thread 0 issues the MMAs and commits each stage to an mbarrier.
+// A stage holds A hi | A lo | B (FWD, DGRAD: the weights) or A hi | A lo | B hi | B lo (WGRAD).
 //
 //   FWD    rows = output positions (n, o)       cols = co   K = (tap, ci)  A = x, B = packed w
 //          out[n][co][o] = b[co] + D, ReLU optional; x may be up-sampled on the fly (nearest,
@@ -84,6 +88,22 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
+// Two FP32 values as two BF16 terms each: *hi = {bf16(a), bf16(b)}, *lo = the BF16 roundings of
+// the remainders a - bf16(a), b - bf16(b) (exact in FP32: the remainder of a rounding to fewer
+// bits of the same value).
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t *hi, uint32_t *lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    *hi = *reinterpret_cast<const uint32_t *>(&h);
+    *lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+// Bytes of one shared-memory stage of a convolution launch with BN columns.
+__host__ __device__ constexpr int conv_stage_bytes(int mode, int bn) {
+    return 2 * (128 * 64 * 2) + (mode == 2 ? 2 : 1) * bn * 128;
+}
+
 // q = t / s for s in {1, 2}; false unless t >= 0, s divides t and q < n
 __device__ __forceinline__ bool exact_div(int t, int s, int n, int &q) {
     if (t < 0) return false;
@@ -115,7 +135,7 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
     const int t = threadIdx.x;
     const int r = t & 127;  // the GEMM row this thread gathers and, in the epilogue, stores
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * bn;
-    const int stage_bytes = kTileA + bn * 128;
+    const int stage_bytes = conv_stage_bytes(MODE, bn);
     uint32_t cols = 32;
     while (cols < (uint32_t)bn) cols <<= 1;
     if (t < 32) gm::tc::tmem_alloc(&tmem_base, cols);
@@ -155,8 +175,10 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
     for (int it = 0; it < nkb; ++it) {
         const int kb = kb0 + it;
         const int s = it & 1;
-        unsigned char *sa = smem + s * stage_bytes;
-        unsigned char *sb = sa + kTileA;
+        unsigned char *sa = smem + s * stage_bytes;  // A hi
+        unsigned char *sal = sa + kTileA;             // A lo
+        unsigned char *sb = sal + kTileA;             // B (hi)
+        unsigned char *sbl = sb + bn * 128;           // B lo (WGRAD)
         if (it >= 2) {  // the MMAs of block it - 2 read this stage
             const bool got = gm::tc::mbar_wait(&bars[s], ((it - 2) >> 1) & 1, p.wait_limit);
             if (__syncthreads_or(!got)) {
@@ -233,9 +255,13 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
                         }
                     }
                 }
-                const uint4 pk = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                                            pack_bf16x2(v[6], v[7]));
-                *reinterpret_cast<uint4 *>(sa + gm::tc::tile_offset(r, kc)) = pk;
+                uint4 ph, pl;
+                split_bf16x2(v[0], v[1], &ph.x, &pl.x);
+                split_bf16x2(v[2], v[3], &ph.y, &pl.y);
+                split_bf16x2(v[4], v[5], &ph.z, &pl.z);
+                split_bf16x2(v[6], v[7], &ph.w, &pl.w);
+                *reinterpret_cast<uint4 *>(sa + gm::tc::tile_offset(r, kc)) = ph;
+                *reinterpret_cast<uint4 *>(sal + gm::tc::tile_offset(r, kc)) = pl;
             }
         } else {
             // WGRAD: warp w fills core column w (positions 8w..8w+7 of the block) of A and B;
@@ -277,7 +303,10 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
                     v[0] = pn[0] >= 0 ? 1.f : 0.f;
                     v[1] = pn[1] >= 0 ? 1.f : 0.f;
                 }
-                *reinterpret_cast<uint32_t *>(sa + gm::tc::tile_offset(row, warp) + 4 * j) = pack_bf16x2(v[0], v[1]);
+                uint32_t h, lo;
+                split_bf16x2(v[0], v[1], &h, &lo);
+                *reinterpret_cast<uint32_t *>(sa + gm::tc::tile_offset(row, warp) + 4 * j) = h;
+                *reinterpret_cast<uint32_t *>(sal + gm::tc::tile_offset(row, warp) + 4 * j) = lo;
             }
             for (int grp = 0; grp < (bn >> 3); ++grp) {  // B rows co
                 const int row = grp * 8 + rr, col = n0 + row;
@@ -287,7 +316,10 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
                     for (int e = 0; e < 2; ++e)
                         if (pn[e] >= 0) v[e] = grad[((size_t)pn[e] * d.CO + col) * osz + po[e]];
                 }
-                *reinterpret_cast<uint32_t *>(sb + gm::tc::tile_offset(row, warp) + 4 * j) = pack_bf16x2(v[0], v[1]);
+                uint32_t h, lo;
+                split_bf16x2(v[0], v[1], &h, &lo);
+                *reinterpret_cast<uint32_t *>(sb + gm::tc::tile_offset(row, warp) + 4 * j) = h;
+                *reinterpret_cast<uint32_t *>(sbl + gm::tc::tile_offset(row, warp) + 4 * j) = lo;
             }
         }
         // ---- B of FWD / DGRAD: bn rows x 8 core columns of packed weights
@@ -304,11 +336,16 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
         __syncthreads();
         if (t == 0) {
             gm::tc::fence_after_sync();
-            const uint32_t a0 = gm::tc::smem_u32(sa), b0 = gm::tc::smem_u32(sb);
+            const uint32_t a0 = gm::tc::smem_u32(sa), al = gm::tc::smem_u32(sal);
+            const uint32_t b0 = gm::tc::smem_u32(sb), bl = gm::tc::smem_u32(sbl);
 #pragma unroll
-            for (int j = 0; j < kTcBK / 16; ++j)
-                gm::tc::mma_bf16(tmem, gm::tc::smem_desc(a0 + j * 256), gm::tc::smem_desc(b0 + j * 256), idesc,
-                                 it > 0 || j > 0);
+            for (int j = 0; j < kTcBK / 16; ++j) {
+                const uint64_t ah = gm::tc::smem_desc(a0 + j * 256), alo = gm::tc::smem_desc(al + j * 256);
+                const uint64_t bh = gm::tc::smem_desc(b0 + j * 256);
+                gm::tc::mma_bf16(tmem, ah, bh, idesc, it > 0 || j > 0);  // hi x hi
+                gm::tc::mma_bf16(tmem, alo, bh, idesc, true);             // lo x hi
+                if (MODE == WGRAD) gm::tc::mma_bf16(tmem, ah, gm::tc::smem_desc(bl + j * 256), idesc, true);  // hi x lo
+            }
             gm::tc::commit(&bars[s]);
         }
         committed = it;
@@ -777,7 +814,7 @@ int launch_tc(const Layer &l, int N, const __nv_bfloat16 *wpk, const float *bias
     int zdim = 1, bn = 16;
     const gm::nn::ConvGemm p = gemm_view<MODE>(l, N, &zdim, &bn);
     const dim3 grid((p.M + 127) / 128, (p.ncols + bn - 1) / bn, zdim);
-    const size_t smem = 2 * ((size_t)gm::nn::kTileA + (size_t)bn * 128);
+    const size_t smem = 2 * (size_t)gm::nn::conv_stage_bytes(MODE, bn);
     gm::nn::k_conv_tc<MODE><<<grid, gm::nn::kTcThreads, smem, s>>>(act, grad, wpk, bias, out, out2, p, bn, err);
     if (MODE == gm::nn::WGRAD || p.ksplit == 1) return 1;
     const int per = MODE == gm::nn::FWD ? l.d.OD * l.d.OH * l.d.OW : l.d.ID * l.d.IH * l.d.IW;
@@ -793,11 +830,12 @@ int wgrad_chunks(const Layer &l, int N) {
 
 cudaError_t set_tc_smem_limits() {
     cudaError_t e = cudaSuccess;
-    for (void *kern : {(void *)gm::nn::k_conv_tc<gm::nn::FWD>, (void *)gm::nn::k_conv_tc<gm::nn::DGRAD>,
-                       (void *)gm::nn::k_conv_tc<gm::nn::WGRAD>})
+    const void *kerns[3] = {(void *)gm::nn::k_conv_tc<gm::nn::FWD>, (void *)gm::nn::k_conv_tc<gm::nn::DGRAD>,
+                            (void *)gm::nn::k_conv_tc<gm::nn::WGRAD>};
+    for (int mode = 0; mode < 3; ++mode)
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     2 * (gm::nn::kTileA + 256 * 128));
+            e = cudaFuncSetAttribute(kerns[mode], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     2 * gm::nn::conv_stage_bytes(mode, 256));
     return e;
 }
 

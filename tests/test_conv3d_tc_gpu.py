@@ -1,9 +1,10 @@
 """The tensor-core convolution kernels one at a time (gm_conv3d) against the oracle's
-convolution of the same BF16-rounded operands summed exactly in float64.
+convolution of the exact FP32 operands with BF16 weights, summed exactly in float64.
 
-Both sides multiply identical BF16 operands, so the only difference is the FP32 accumulation
-of the tensor cores over K = 9 or 27 taps x up to 512 channels (or over all positions for the
-weight gradient): a relative 2-norm error of order 1e-6; the bound is 1e-5.  The geometries
+The kernels carry each FP32 activation and gradient as two BF16 terms (hi + lo: rms relative
+representation error about 1.3e-6) and accumulate the products in FP32 over K = 9 or 27 taps x
+up to 512 channels (or over all positions for the weight gradient, whose lo x lo term is left
+out, about 1.3e-6 of each product): a relative 2-norm error of order 2e-6; the bound is 1e-5.  The geometries
 cover one input channel, one output channel, odd sizes that leave ragged 128-row tiles,
 stride 2, 3-D kernels and two 256-column tiles.
 """
@@ -11,7 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import warmstart_net as N
-from tests.conftest import rel_err
+from tests.conftest import assert_close, rel_err
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -59,13 +60,13 @@ def test_conv_modes_match_bf16_operand_oracle(ws, geom):
     x, g, w, b = _data(geom, 1)
     st = geom[7]
     out = ws.conv3d(0, _cuda(w), x=_cuda(x), b=_cuda(b), stride=st).cpu().numpy()
-    assert rel_err(out, N.conv_bf16(0, w, x=x, b=b, stride=st)) < TOL
+    assert rel_err(out, N.conv_bf16(0, w, x=x, b=b, stride=st, round_operands=False)) < TOL
     dx = torch.empty(x.shape, dtype=torch.float32, device="cuda")
     ws.conv3d(1, _cuda(w), g=_cuda(g), stride=st, out=dx)
-    assert rel_err(dx.cpu().numpy(), N.conv_bf16(1, w, g=g, stride=st, in_shape=x.shape)) < TOL
+    assert rel_err(dx.cpu().numpy(), N.conv_bf16(1, w, g=g, stride=st, in_shape=x.shape, round_operands=False)) < TOL
     db = torch.empty(geom[2], dtype=torch.float32, device="cuda")
     dw = ws.conv3d(2, _cuda(w), x=_cuda(x), g=_cuda(g), stride=st, bias_grad=db).cpu().numpy()
-    ref_w, ref_b = N.conv_bf16(2, w, x=x, g=g, stride=st)
+    ref_w, ref_b = N.conv_bf16(2, w, x=x, g=g, stride=st, round_operands=False)
     assert rel_err(dw, ref_w) < TOL
     assert rel_err(db.cpu().numpy(), ref_b) < TOL
 
@@ -75,7 +76,7 @@ def test_conv_without_bias_and_bad_arguments(ws, gm):
 
     x, g, w, b = _data(GEOMS[1], 2)
     out = ws.conv3d(0, _cuda(w), x=_cuda(x), stride=2).cpu().numpy()
-    assert rel_err(out, N.conv_bf16(0, w, x=x, stride=2)) < TOL
+    assert rel_err(out, N.conv_bf16(0, w, x=x, stride=2, round_operands=False)) < TOL
     w3 = torch.zeros((64, 24, 1, 3, 3), device="cuda")  # 24 input channels: not a power of two
     with pytest.raises(gm.GravMagError, match="powers of two"):
         ws.conv3d(0, w3, x=torch.zeros((1, 24, 1, 8, 8), device="cuda"))

@@ -1,26 +1,33 @@
 """The warm-start network's tensor-core kernels against the float64 CPU oracle of the network.
 
-Every convolution is a tcgen05 GEMM of BF16 operands (the BF16 weights, and the FP32
-activations and gradients rounded to BF16 as they are gathered) with FP32 accumulation; one
-convolution at a time agrees with the oracle to 1e-6 (tests/test_conv3d_tc_gpu.py).  Through
-the whole network the comparison is bounded by the BF16 rounding itself: the oracle rounds the
-same operands (``bf16_operands=True``), but an FP32-vs-float64 difference of 1e-7 in any sum
-moves some operand across a BF16 rounding boundary, and the 18 products of a step spread that
-to every output.  Perturbing the oracle's own sums by a relative 1e-7 moves its output by about
-4e-3 and its gradient by a few 1e-2 (on the networks tested here), the same size as the
-difference between BF16 and exact operands (5e-3 and 3e-2).  The bounds are TOL_FWD = 2e-2 on
-outputs and TOL_GRAD = 1e-1 on gradients (0.2 per layer); an indexing error gives O(1).
+Every convolution is a tcgen05 GEMM with BF16 weights and FP32 accumulation; the FP32
+activations and gradients enter as two BF16 terms each (hi + lo), so the products are those of
+the FP32 values to a relative 1e-6 (one convolution at a time against the oracle's exact
+operands: tests/test_conv3d_tc_gpu.py, 1e-5).  The oracle here runs the network in float64 with
+the same BF16 weights and exact activations and gradients.  Through the nine layers of the
+forward pass and the eighteen products of a training step the differences stay at the level of
+the FP32 sums and the two-term operands (a few 1e-6); the bounds are 1e-4 on outputs, on the
+whole gradient and on the loss, and 1e-3 on every layer's weight and bias gradients.  An
+indexing error gives O(1).
+
+The gradient jumps where a ReLU input changes sign, so the gradient tests use inputs whose ReLU
+inputs all clear zero by KINK_MARGIN of their layer's rms in the oracle (found by scanning input
+seeds), about three times the spread of the per-value differences.  Without it a single ReLU
+input within 1e-6 of zero takes opposite sides in the two computations and moves the gradients
+upstream of it by ~1e-3 (observed on the 16 x 16 grid for one seed).
 """
 import numpy as np
 import pytest
 
 from oracle import warmstart_net as N
-from tests.conftest import rel_err
+from tests.conftest import assert_close, rel_err
 
 pytestmark = pytest.mark.gpu
-TOL_FWD = 2e-2
-TOL_GRAD = 1e-1
-TOL_LOSS = 1e-3
+TOL_FWD = 1e-4
+TOL_GRAD = 1e-4
+TOL_LAYER = 1e-3
+TOL_LOSS = 1e-4
+KINK_MARGIN = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -43,6 +50,17 @@ def _cuda(a):
     return torch.as_tensor(np.ascontiguousarray(a)).cuda()
 
 
+def _kink_free_inputs(net, S, batch, in_scale, seed0, tries=80):
+    """The first of _inputs(S, batch, seed0 + k) whose ReLU inputs all clear zero by KINK_MARGIN
+    (relative to each layer's rms) in the oracle with the network's BF16 weights."""
+    p = N.conv_weights_bf16(net.get_params())
+    for seed in range(seed0, seed0 + tries):
+        d, m = _inputs(S, batch, seed)
+        if N.relu_margin(p, d.astype(np.float64), in_scale) > KINK_MARGIN:
+            return d, m
+    pytest.fail(f"no input of {tries} seeds clears the ReLU kinks by {KINK_MARGIN}")
+
+
 def test_parameter_count(ws):
     net = ws.WarmStartNet(grid=32, max_batch=2, seed=0)
     assert net.num_params == N.num_params() == 1858849
@@ -56,10 +74,9 @@ def test_forward_matches_oracle(ws, S, batch):
     d, _ = _inputs(S, batch, 1)
     got = net.forward(_cuda(d)).cpu().numpy()
     p = N.conv_weights_bf16(net.get_params())
-    ref = N.forward(p, d.astype(np.float64), 0.8, 1.7, bf16_operands=True)
+    ref = N.forward(p, d.astype(np.float64), 0.8, 1.7)
     assert got.shape == (batch, 16, S, S)
-    err = rel_err(got, ref)
-    assert err < TOL_FWD, err
+    assert_close(got, ref, TOL_FWD)
     # gather + scale, 9 convolutions (up-sampling folded in), their split-K finishes, output scale
     assert 11 <= net.last_launch_count() <= 20
     net.close()
@@ -74,19 +91,19 @@ def _layer_slices():
     return out
 
 
-@pytest.mark.parametrize("S", [16, 32])
-def test_loss_and_gradient_match_oracle(ws, S):
+@pytest.mark.parametrize("S,batch", [(16, 3), (32, 1)])
+def test_loss_and_gradient_match_oracle(ws, S, batch):
     net = ws.WarmStartNet(grid=S, max_batch=4, seed=3)
     net.set_scales(1.1, 0.6)
-    d, m = _inputs(S, 3, 2)
+    d, m = _kink_free_inputs(net, S, batch, 1.1, 2)
     loss = net.train_step(_cuda(d), _cuda(m), 0.0)
     g = net.get_params("grad").astype(np.float64)
     p = N.conv_weights_bf16(net.get_params())
-    ref_loss, ref_g = N.loss_and_grad(p, d.astype(np.float64), m.astype(np.float64), 1.1, 0.6, bf16_operands=True)
+    ref_loss, ref_g = N.loss_and_grad(p, d.astype(np.float64), m.astype(np.float64), 1.1, 0.6)
     assert abs(loss - ref_loss) <= TOL_LOSS * ref_loss
     per_layer = [(rel_err(g[ws_], ref_g[ws_]), rel_err(g[bs], ref_g[bs])) for ws_, bs in _layer_slices()]
     assert rel_err(g, ref_g) < TOL_GRAD, per_layer
-    assert max(max(e) for e in per_layer) < 2 * TOL_GRAD, per_layer  # every layer's weights and biases
+    assert max(max(e) for e in per_layer) < TOL_LAYER, per_layer  # every layer's weights and biases
     assert net.step == 0  # lr = 0: no Adam step
     net.close()
 
@@ -177,7 +194,7 @@ def test_training_is_deterministic(ws):
 
 def test_data_term_loss_and_gradient_match_oracle(ws, gm):
     """Training with the data-consistency term: the library's FP32 G / G^T inside the train step
-    against the dense long-double G of the prism oracle inside the float64 network oracle."""
+    against the dense binary128 G of the prism oracle inside the float64 network oracle."""
     import oracle as O
 
     S = 16
@@ -187,14 +204,13 @@ def test_data_term_loss_and_gradient_match_oracle(ws, gm):
     net = ws.WarmStartNet(grid=S, max_batch=4, seed=11)
     net.set_scales(0.3, 0.8)
     net.set_data_term(op, 0.5)
-    d, m = _inputs(S, 3, 9)
+    d, m = _kink_free_inputs(net, S, 3, 0.3, 9)
     loss = net.train_step(_cuda(d), _cuda(m), 0.0)
     model_term, data_term = net.last_losses()
     g = net.get_params("grad").astype(np.float64)
     p = N.conv_weights_bf16(net.get_params())
-    ref_loss, ref_g = N.loss_and_grad(p, d.astype(np.float64), m.astype(np.float64), 0.3, 0.8, Gd, 0.5,
-                                      bf16_operands=True)
-    ref_model = N.loss(p, d.astype(np.float64), m.astype(np.float64), 0.3, 0.8, bf16_operands=True)
+    ref_loss, ref_g = N.loss_and_grad(p, d.astype(np.float64), m.astype(np.float64), 0.3, 0.8, Gd, 0.5)
+    ref_model = N.loss(p, d.astype(np.float64), m.astype(np.float64), 0.3, 0.8)
     assert abs(model_term - ref_model) <= TOL_LOSS * ref_model
     assert abs(loss - ref_loss) <= TOL_LOSS * ref_loss
     assert abs(loss - (model_term + 0.5 * data_term)) <= 1e-6 * loss

@@ -201,3 +201,24 @@ def test_bf16_operand_gradient_is_close_to_the_exact_one():
     _, g2 = N.loss_and_grad(p, d, m, bf16_operands=True)
     rel = np.linalg.norm(g1 - g2) / np.linalg.norm(g1)
     assert 1e-4 < rel < 1e-1
+
+
+def test_relu_margin_is_the_smallest_relu_input_over_its_layer_rms():
+    """With all weights zero every ReLU input equals its channel's bias at every position, so
+    the margin is min over ReLU layers of min_c |b_c| / sqrt(mean_c b_c^2) (each channel has the
+    same number of positions); layer 3 gets one small bias, which must set the margin."""
+    p = np.zeros(N.num_params())
+    off, expect = 0, []
+    for li, (ci, co, kd, _, _, relu) in enumerate(N.LAYERS):
+        off += co * ci * kd * 9
+        b = 0.5 + np.arange(co, dtype=np.float64) / co
+        if li == 3:
+            b[7] = 0.003
+        p[off:off + co] = b
+        off += co
+        if relu:
+            expect.append(np.min(np.abs(b)) / np.sqrt(np.mean(b * b)))
+    d = np.random.default_rng(0).standard_normal((2, 16, 16))
+    got = N.relu_margin(p, d)
+    assert got == pytest.approx(min(expect), rel=1e-12)
+    assert int(np.argmin(expect)) == 3  # the small bias of layer 3 sets it
