@@ -366,9 +366,11 @@ def time_steps(op, m, d, outd, outm, flush, steps):
     return [s.elapsed_time(e) for s, e in zip(starts, ends)]
 
 
-def capture_steps(op, m, d, outd, outm, flush, steps):
+def capture_steps(op, m, d, outd, outm, flush, steps, concurrent=False):
     """One CUDA graph holding `steps` steps (flush, start event, forward, transpose, end event) so
-    that the timed replay measures device time without host launch gaps.  Returns
+    that the timed replay measures device time without host launch gaps.  With concurrent, each
+    step's forward and transpose (independent products; the handle gives each its own workspace)
+    run on two streams that fork after the start event and join before the end event.  Returns
     (graph, starts, ends) or None when this torch cannot record timing events inside a graph."""
     import torch
 
@@ -378,14 +380,20 @@ def capture_steps(op, m, d, outd, outm, flush, steps):
     except TypeError:
         return None
     g = torch.cuda.CUDAGraph()
-    cs = torch.cuda.Stream()
+    cs, ts = torch.cuda.Stream(), torch.cuda.Stream()
     cs.wait_stream(torch.cuda.current_stream())
     with torch.cuda.graph(g, stream=cs):
         for k in range(steps):
             flush.fill_(k & 0xFF)
             starts[k].record()
-            op.forward(m, out=outd)
-            op.transpose(d, out=outm)
+            if concurrent:
+                ts.wait_stream(cs)
+                op.forward(m, out=outd)
+                op.transpose(d, out=outm, stream=ts)
+                cs.wait_stream(ts)
+            else:
+                op.forward(m, out=outd)
+                op.transpose(d, out=outm)
             ends[k].record()
     torch.cuda.synchronize()
     return g, starts, ends
@@ -414,11 +422,21 @@ def run_ours(args):
     time_steps(op, m, d, outd, outm, flush, max(args.warmup, 3))
     # the headline graph holds no per-kernel timing events (an event between two launches would
     # serialise them fully instead of letting the next kernel's launch overlap the previous tail)
-    cap = capture_steps(op, m, d, outd, outm, flush, args.steps)
+    cap = capture_steps(op, m, d, outd, outm, flush, args.steps, concurrent=True)
     if cap is not None:
         graph, starts, ends = cap
         graph.replay()  # warm replay; the timed replay re-records the same timing events
         torch.cuda.synchronize()
+    # the same steps with forward and transpose one after the other on one stream, for reference
+    cap_s = capture_steps(op, m, d, outd, outm, flush, args.steps, concurrent=False)
+    serial_ms = None
+    if cap_s is not None:
+        cap_s[0].replay()
+        torch.cuda.synchronize()
+        cap_s[0].replay()
+        torch.cuda.synchronize()
+        serial_ms = [a.elapsed_time(b) for a, b in zip(cap_s[1], cap_s[2])]
+        del cap_s
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
@@ -427,7 +445,8 @@ def run_ours(args):
         graph.replay()
         torch.cuda.synchronize()
         per_step = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-        timing_mode = "one CUDA graph of all timed steps (no host launch gaps)"
+        timing_mode = ("one CUDA graph of all timed steps (no host launch gaps); each step's forward and "
+                       "transpose, independent products, on two streams")
     else:
         per_step = time_steps(op, m, d, outd, outm, flush, args.steps)
         timing_mode = "eager launches"
@@ -577,6 +596,10 @@ def run_ours(args):
                                 "apply_equivalent_per_s": 2.0 / (per_it / 1e3),
                                 "fft": f"{opc.info.fft_nx}x{opc.info.fft_ny}"}
         opc.close()
+    if serial_ms:
+        extra["serial"] = {"value": 2.0 * len(serial_ms) / (sum(serial_ms) / 1e3), "unit": UNIT,
+                           "ms_per_step": sum(serial_ms) / len(serial_ms),
+                           "timing": "the same graph with forward and transpose on one stream"}
     extra["setup_ms"] = inf.setup_ms
     extra["kernel_ms_per_step"] = {k: v[1] / args.steps for k, v in ktimes.items()}
     extra["ms_per_step_with_kernel_events"] = ms_per_step_with_kernel_events

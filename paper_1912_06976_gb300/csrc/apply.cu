@@ -104,8 +104,8 @@ template <typename R>
 static cudaError_t transpose_t(gm_plan *p, const R *d, R *m, cudaStream_t s, int *nl) {
     using C = cpx_t<R>;
     const Geo &g = p->geo;
-    C *D1 = reinterpret_cast<C *>(p->work_small);
-    C *A2 = reinterpret_cast<C *>(p->work_big);
+    C *D1 = reinterpret_cast<C *>(p->work_small_tr);
+    C *A2 = reinterpret_cast<C *>(p->work_big_tr);
     const C *S = reinterpret_cast<const C *>(p->spec);
     allow_smem(k_rows_r2c<C, R>, 2 * sizeof(C) * g.NPx);
     allow_smem(k_tr_cols<C>, 3 * sizeof(C) * g.NPy);

@@ -66,8 +66,8 @@ template <typename R>
 cudaError_t transpose_fast_t(gm_plan *p, const io_t<R> *d, io_t<R> *m, cudaStream_t s, int *nl) {
     using C = cpx_t<R>;
     const Geo &g = p->geo;
-    C *D1 = static_cast<C *>(p->work_small);
-    C *A2 = static_cast<C *>(p->work_big);
+    C *D1 = static_cast<C *>(p->work_small_tr);
+    C *A2 = static_cast<C *>(p->work_big_tr);
     const C *S = static_cast<const C *>(p->spec);
     int t = timing_begin(p, s, K_TR_ROWS);
     const XOps<R> *xo = x_ops<R>(g.NPx);

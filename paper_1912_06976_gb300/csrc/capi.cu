@@ -137,6 +137,8 @@ static void free_plan(gm_plan *p) {
     cudaFree(p->spec);
     cudaFree(p->work_big);
     cudaFree(p->work_small);
+    cudaFree(p->work_big_tr);
+    cudaFree(p->work_small_tr);
     cudaFree(p->work_part);
     cudaFree(p->work_counters);
     cudaFree(p->stage_m);
@@ -302,7 +304,7 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
         part = cel * (size_t)p->fast_groups_fwd * g.Kx * g.NPy;
         ncount = (size_t)gm::fast_column_groups(p);
     }
-    p->work_bytes = big + small + part + rel * (n_model + n_data);
+    p->work_bytes = 2 * (big + small) + part + rel * (n_model + n_data);
     const size_t setup_peak = sizeof(double) * ((size_t)(p->Nx + 1) * (p->Ny + 1) * g.nz +
                                                 (size_t)g.NPx * g.NPy * g.nz) +
                               sizeof(double2) * nspec + 4 * sizeof(double2) * (g.NPx + g.NPy);
@@ -335,6 +337,8 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
     SETUP_TRY(cudaMalloc(&p->spec, p->spec_bytes), "spectra");
     SETUP_TRY(cudaMalloc(&p->work_big, big), "workspace");
     SETUP_TRY(cudaMalloc(&p->work_small, small), "workspace");
+    SETUP_TRY(cudaMalloc(&p->work_big_tr, big), "workspace");
+    SETUP_TRY(cudaMalloc(&p->work_small_tr, small), "workspace");
     if (part) SETUP_TRY(cudaMalloc(&p->work_part, part), "workspace");
     if (ncount) {
         SETUP_TRY(cudaMalloc(&p->work_counters, sizeof(unsigned int) * ncount), "workspace");

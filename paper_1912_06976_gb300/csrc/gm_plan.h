@@ -32,8 +32,11 @@ struct gm_plan {
     bool spec_real = false;
 
     // Workspace: the large intermediate (forward [Kx][nz][ny], transpose [nz][ny][Kx]),
-    // the small one (forward [sy][Kx], transpose [Kx][sy]) and host-call staging.
-    void *work_big = nullptr, *work_small = nullptr;
+    // the small one (forward [sy][Kx], transpose [Kx][sy]) and host-call staging.  The forward
+    // and the transpose each have their own pair, so that one of each may run at the same time
+    // on different streams.
+    void *work_big = nullptr, *work_small = nullptr;        // forward
+    void *work_big_tr = nullptr, *work_small_tr = nullptr;  // transpose
     void *stage_m = nullptr, *stage_d = nullptr;
     size_t work_bytes = 0;
 

@@ -377,3 +377,30 @@ def test_df64_needs_register_codelet_lengths(gm, monkeypatch):
     monkeypatch.setenv("GM_GENERIC_FFT", "1")
     with pytest.raises(gm.GravMagError, match="GM_DF64"):
         gm.Operator(16, 16, 2, 10.0, 10.0, 10.0, precision=gm.DF64)
+
+
+@pytest.mark.parametrize("name,prec", [("grav300", 0), ("mag64", 1), ("mag64", 2), ("grav16", 0)])
+def test_forward_and_transpose_overlap_on_two_streams(gm, name, prec):
+    """A forward and a transpose product of one handle may run at the same time on two streams
+    (each has its own workspace): every result equals the serial one bit for bit."""
+    import torch
+
+    w = W.WORKLOADS[name]
+    op = gm.Operator.from_workload(w, precision=prec)
+    dt = op.dtype
+    m = torch.as_tensor(W.model(name, 0), dtype=dt, device="cuda").contiguous()
+    d = torch.as_tensor(W.data(name, 0), dtype=dt, device="cuda").contiguous()
+    ref_d = op.forward(m).clone()
+    ref_m = op.transpose(d).clone()
+    sf, st = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = [(torch.empty(op.data_shape, dtype=dt, device="cuda"), torch.empty(op.model_shape, dtype=dt, device="cuda"))
+            for _ in range(4)]
+    sf.wait_stream(torch.cuda.current_stream())
+    st.wait_stream(torch.cuda.current_stream())
+    for od, om in outs:
+        op.forward(m, out=od, stream=sf)
+        op.transpose(d, out=om, stream=st)
+    torch.cuda.synchronize()
+    for od, om in outs:
+        assert torch.equal(od, ref_d) and torch.equal(om, ref_m)
+    op.close()
