@@ -15,7 +15,18 @@
 //     gives the entry k_r(delta) (Sec. 4.1: g = CM(1:,1:) - CM(1:,2:) - ...);
 //     entry k_r(delta) with delta = -u - pxl is written at generator position
 //     (u mod N'_x, v mod N'_y) for u in [-(nx-1), sx-1] (Eqs. Tcircpadded,
-//     Tcircpaddedgeneral), zeros elsewhere.
+//     Tcircpaddedgeneral), zeros elsewhere.  That difference cancels by about
+//     (r / cell)^2 at distance r (~1e-13 relative error in FP64 for the far and
+//     deep cells of a 300 x 250 x 60 grid), so cells whose horizontal gap to the
+//     station is at least 2.5 cell widths (2.5 layer thicknesses too, for the
+//     magnetic kernel) take instead the defining integral by Gauss-Legendre
+//     quadrature, which has no cancellation there: gravity, gamma times the
+//     (x, y) face integral of the depth integral of z / r^3, 1/r1 - 1/r2 =
+//     (z2^2 - z1^2) / (r1 r2 (r1 + r2)), with 8 x 8 nodes; magnetic, F / 4pi
+//     times the volume integral of Fhat . (grad grad 1/r) . Fhat =
+//     (3 (Fhat . r)^2 - r^2) / r^5 with 8 x 8 x 8 nodes.  The integrands'
+//     nearest singularity, at the station, is at least five half cell widths
+//     away, which bounds the quadrature error near 1e-16.
 //  K3 2-D FFT of each generator in FP64 (rows, then columns), then rounding
 //     to the apply precision.
 #include <cstring>
@@ -91,8 +102,69 @@ __global__ void k_corner_columns(double *__restrict__ Q, CornerArgs a) {
     Q[((size_t)r * a.ncy + iy) * a.ncx + ix] = q;
 }
 
-// K2: generator T[r][vy][ux] (real, FP64) from the corner columns.
-__global__ void k_generator(const double *__restrict__ Q, double *__restrict__ T, Geo g, int ncx, int ncy) {
+// Far-field quadrature of the entries (K2): quad = 1 gravity (face integral), 2 magnetic (volume
+// integral), 0 none; cells whose horizontal gap to the station is at least gap_cells cell widths
+// (and, for the magnetic kernel, as many layer thicknesses) use the GL nodes x[] and weights w[]
+// on [-1, 1]; the others keep the 4-point corner difference.
+constexpr int kFarNodes = 8;
+constexpr double kPiSetup = 3.14159265358979323846264338327950288;
+struct FarField {
+    int quad;
+    double gap_cells;
+    double x0, y0, dx, dy, gamma;  // corner 0 of the offset grid, cell sizes, gravity constant
+    double H, l, m, n;             // magnetic: F / 4pi and the direction cosines of Fhat
+    const double *z;
+    double x[kFarNodes], w[kFarNodes];
+};
+
+// (F / 4pi) * integral over the cell of (3 (Fhat . r)^2 - r^2) / r^5 (Sec. 4.2's entry, the
+// induced dipole field along Fhat)
+__device__ double mag_volume_quadrature(const FarField &f, double xl, double yl, double z1, double z2) {
+    const double hx = 0.5 * f.dx, hy = 0.5 * f.dy, hz = 0.5 * (z2 - z1);
+    const double cx = xl + hx, cy = yl + hy, cz = z1 + hz;
+    double s = 0.0;
+    for (int i = 0; i < kFarNodes; ++i) {
+        const double x = cx + hx * f.x[i];
+        for (int j = 0; j < kFarNodes; ++j) {
+            const double y = cy + hy * f.x[j];
+            const double u = f.l * x + f.m * y, rho2 = x * x + y * y;
+            double sk = 0.0;
+#pragma unroll
+            for (int k = 0; k < kFarNodes; ++k) {
+                const double z = cz + hz * f.x[k];
+                const double r2 = rho2 + z * z, t = u + f.n * z;
+                sk += f.w[k] * (3.0 * t * t - r2) / (r2 * r2 * sqrt(r2));
+            }
+            s += f.w[i] * f.w[j] * sk;
+        }
+    }
+    return f.H * s * hx * hy * hz;
+}
+
+// gamma * integral over [xl, xl + dx] x [yl, yl + dy] of (z2^2 - z1^2) / (r1 r2 (r1 + r2)),
+// r_k = sqrt(x^2 + y^2 + z_k^2): the depth integral of z / r^3 over [z1, z2] (Sec. 4.1's entry)
+__device__ double grav_face_quadrature(const FarField &f, double xl, double yl, double z1, double z2) {
+    const double hx = 0.5 * f.dx, hy = 0.5 * f.dy, cx = xl + hx, cy = yl + hy;
+    const double dz2 = (z2 - z1) * (z2 + z1), a1 = z1 * z1, a2 = z2 * z2;
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < kFarNodes; ++i) {
+        const double x = cx + hx * f.x[i], x2 = x * x;
+        double si = 0.0;
+#pragma unroll
+        for (int j = 0; j < kFarNodes; ++j) {
+            const double y = cy + hy * f.x[j], R2 = x2 + y * y;
+            const double r1 = sqrt(R2 + a1), r2 = sqrt(R2 + a2);
+            si += f.w[j] / (r1 * r2 * (r1 + r2));
+        }
+        s += f.w[i] * si;
+    }
+    return f.gamma * dz2 * s * hx * hy;
+}
+
+// K2: generator T[r][vy][ux] (real, FP64) from the corner columns, or by quadrature far out.
+__global__ void k_generator(const double *__restrict__ Q, double *__restrict__ T, Geo g, int ncx, int ncy,
+                            FarField f) {
     const int ux = blockIdx.x * blockDim.x + threadIdx.x;
     const int vy = blockIdx.y;
     const int r = blockIdx.z;
@@ -103,11 +175,46 @@ __global__ void k_generator(const double *__restrict__ Q, double *__restrict__ T
     if (u >= -(g.nx - 1) && v >= -(g.ny - 1)) {
         // corner index of the lower x edge of offset delta_x = -u - pxl:  sx - 1 - u
         const int xi = g.sx - 1 - u, yi = g.sy - 1 - v;
-        const double *Qr = Q + (size_t)r * ncy * ncx;
-        t = Qr[(size_t)(yi + 1) * ncx + xi + 1] - Qr[(size_t)(yi + 1) * ncx + xi] -
-            Qr[(size_t)yi * ncx + xi + 1] + Qr[(size_t)yi * ncx + xi];
+        const int ddx = -u - g.pxl, ddy = -v - g.pyl;  // cell offset from the station, in cells
+        // horizontal gap between the station and the cell (a lower bound of their distance)
+        const double gap = fmax((abs(ddx) - 0.5) * f.dx, (abs(ddy) - 0.5) * f.dy);
+        const double z1 = f.z[r], z2 = f.z[r + 1];
+        double scale = fmax(f.dx, f.dy);
+        if (f.quad == 2) scale = fmax(scale, z2 - z1);
+        if (f.quad && gap >= f.gap_cells * scale) {
+            t = f.quad == 1 ? grav_face_quadrature(f, f.x0 + xi * f.dx, f.y0 + yi * f.dy, z1, z2)
+                            : mag_volume_quadrature(f, f.x0 + xi * f.dx, f.y0 + yi * f.dy, z1, z2);
+        } else {
+            const double *Qr = Q + (size_t)r * ncy * ncx;
+            t = Qr[(size_t)(yi + 1) * ncx + xi + 1] - Qr[(size_t)(yi + 1) * ncx + xi] -
+                Qr[(size_t)yi * ncx + xi + 1] + Qr[(size_t)yi * ncx + xi];
+        }
     }
     T[((size_t)r * g.NPy + vy) * g.NPx + ux] = t;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton's iteration on the Legendre polynomial
+// P_n from the Chebyshev-like first guesses, in long double), rounded to double.
+static void gauss_legendre(int n, double *x, double *w) {
+    const long double pi = 3.14159265358979323846264338327950288L;
+    for (int i = 0; i < n; ++i) {
+        long double t = cosl(pi * ((long double)i + 0.75L) / ((long double)n + 0.5L));
+        long double dp = 1.0L;
+        for (int it = 0; it < 100; ++it) {
+            long double p0 = 1.0L, p1 = t;  // P_0, P_1
+            for (int k = 2; k <= n; ++k) {
+                const long double pk = ((2.0L * k - 1.0L) * t * p1 - (k - 1.0L) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            dp = n * (t * p1 - p0) / (t * t - 1.0L);  // P_n'(t)
+            const long double dt = p1 / dp;
+            t -= dt;
+            if (fabsl(dt) <= 1e-19L * fabsl(t)) break;
+        }
+        x[i] = (double)t;
+        w[i] = (double)(2.0L / ((1.0L - t * t) * dp * dp));
+    }
 }
 
 __global__ void k_round_to_f32(const double2 *__restrict__ in, float2 *__restrict__ out, size_t n) {
@@ -205,8 +312,25 @@ cudaError_t build_spectra(gm_plan *p, cudaStream_t s) {
         GM_TRY(cudaGetLastError());
     }
     {
+        FarField f{};
+        f.quad = p->kind == GM_GRAVITY ? 1 : 2;
+        f.gap_cells = 2.5;
+        {
+            const double I = p->incl_deg * kPiSetup / 180.0, D = p->decl_deg * kPiSetup / 180.0;
+            f.l = std::cos(I) * std::cos(D);
+            f.m = std::cos(I) * std::sin(D);
+            f.n = std::sin(I);
+            f.H = p->F_nT / (4.0 * kPiSetup);
+        }
+        f.x0 = ((double)(-(g.sx - 1 + g.pxl)) - 0.5) * p->dx;
+        f.y0 = ((double)(-(g.sy - 1 + g.pyl)) - 0.5) * p->dy;
+        f.dx = p->dx;
+        f.dy = p->dy;
+        f.gamma = p->coef[0];
+        f.z = z;
+        gauss_legendre(kFarNodes, f.x, f.w);
         dim3 blk(128), grd((g.NPx + 127) / 128, g.NPy, g.nz);
-        k_generator<<<grd, blk, 0, s>>>(Q, T, g, ncx, ncy);
+        k_generator<<<grd, blk, 0, s>>>(Q, T, g, ncx, ncy, f);
         GM_TRY(cudaGetLastError());
     }
     {

@@ -126,18 +126,19 @@ def test_full_size_sampled_vs_oracle(gm, name, prec):
     assert_close(tr.ravel()[g["transpose_cells"]], g["transpose"], TOL[prec])
 
 
+@pytest.mark.parametrize("name", ["mag64", "grav300", "mag128"])
 @pytest.mark.parametrize("prec", [1, 2])
-def test_full_size_fp64_error_levels(gm, prec):
-    """The FP64 and double-float products on the 300x250x60 grid against the binary128 oracle
-    samples, well inside the 1e-12 gate: the forward at rounding level (5e-16 FP64, 6e-15
-    double-float measured), the transpose at the level of the FP64 set-up entries' rounding
-    (1.1e-13 measured: a white data vector weights the deep and far entries, whose 4-point
-    corner differences cancel by about (r / cell)^2)."""
-    g = _golden("grav300")
-    w = W.WORKLOADS["grav300"]
-    fwd, tr = run(gm, w, prec, W.model("grav300", g["model_seed"]), W.data("grav300", g["data_seed"]))
+def test_full_size_fp64_error_levels(gm, name, prec):
+    """The FP64 and double-float products of the full-size workloads against the binary128
+    oracle samples, far inside the 1e-12 gate: 4e-16 to 6e-16 measured in FP64 and 1e-15 to
+    9e-15 in double-float, forward and transpose.  (With the far-field entries taken from the
+    4-point corner difference, which cancels by about (r / cell)^2, the 300x250x60 transpose
+    was 1.1e-13 off: a white data vector weights the deep and far entries.)"""
+    g = _golden(name)
+    w = W.WORKLOADS[name]
+    fwd, tr = run(gm, w, prec, W.model(name, g["model_seed"]), W.data(name, g["data_seed"]))
     assert_close(fwd.ravel()[g["forward_stations"]], g["forward"], 2e-14)
-    assert_close(tr.ravel()[g["transpose_cells"]], g["transpose"], 4e-13)
+    assert_close(tr.ravel()[g["transpose_cells"]], g["transpose"], 2e-14)
 
 
 @pytest.mark.parametrize("name", ["mag64", "grav300"])
@@ -293,13 +294,9 @@ def test_gravity_real_spectra_match_complex_spectra(gm, monkeypatch, name, prec)
     assert op.info.spectrum_real == 1
     op.close()
     got_f, got_t = run(gm, w, prec, m, d)
-    # FP64 / DF64: the real even form keeps Re(w conj(T)), i.e. it averages the FP64 entries
-    # k(dx, dy) and k(-dx, dy), which agree exactly in exact arithmetic (the gravity kernel is even,
-    # Sec. 2.2.3) but differ in FP64 by the rounding of the entries' 4-point corner difference,
-    # about (r / cell)^2 eps relative for a cell at distance r: ~1e-13 in the deep layers of the
-    # 300x250x60 grid.  A white data vector sums those errors incoherently in the transpose
-    # (measured 1.3e-13 between the two forms, each ~1.1e-13 from the binary128 oracle).
-    tol = 2e-6 if prec == 0 else 5e-13
+    # FP64 / DF64: two forms of the same FP64 entries, differing by rounding (5e-16 FP64 and
+    # 6e-15 double-float measured on the 300x250x60 grid)
+    tol = 2e-6 if prec == 0 else 1e-13
     assert_close(got_f, ref_f, tol)
     assert_close(got_t, ref_t, tol)
 
