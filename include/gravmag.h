@@ -33,12 +33,14 @@
  * nothing, do not synchronise (except the *_host variants) and are ordered on
  * the CUDA stream passed in (NULL = the legacy default stream).  The forward
  * and the transpose products of a handle have separate workspaces: one
- * apply_forward and one apply_transpose may run at the same time on two
- * streams (independent products, e.g. G m and G^T d of one step).  Other calls
- * on one handle must not overlap in time: two forwards, two transposes, the
- * host-buffer variants (one staging area) and gm_cgls / gm_cgls_noalloc
- * (which use both products); serialise them on one stream.  Distinct handles
- * are independent.
+ * forward and one transpose (apply_forward / apply_transpose, or their
+ * host-buffer variants with page-locked buffers, e.g. from two host threads)
+ * may run at the same time on two streams (independent products, e.g. G m and
+ * G^T d of one step).  Other calls on one handle must not overlap in time: two
+ * forwards, two transposes, host-buffer variants with pageable buffers (one
+ * staging area), gm_cgls / gm_cgls_noalloc (which use both products), and any
+ * call while per-kernel timing is enabled; serialise them on one stream.
+ * Distinct handles are independent.
  *
  * Errors: every call returns a gm_status (setup returns NULL and sets the
  * thread's last status).  No call faults the process on bad arguments.

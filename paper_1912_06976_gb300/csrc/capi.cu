@@ -588,7 +588,7 @@ const char *gm_status_string(gm_status s) {
     return "unknown gm_status";
 }
 
-int gm_last_launch_count(gm_handle h) { return h ? h->last_launches : 0; }
+int gm_last_launch_count(gm_handle h) { return h ? h->last_launches.load() : 0; }
 
 gm_status gm_enable_timing(gm_handle h, int capacity) {
     if (!h || capacity < 0) return fail(GM_EINVAL, "bad handle or capacity");

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <atomic>
 #include <vector>
 
 #include "../../include/gravmag.h"
@@ -52,7 +53,7 @@ struct gm_plan {
     size_t cgls_bytes = 0;
 
     double setup_ms = 0;
-    int last_launches = 0;
+    std::atomic<int> last_launches{0};  // written by concurrent forward and transpose calls
 
     // Optional per-kernel timing: event pairs around each launch (see gm_enable_timing).
     std::vector<cudaEvent_t> tev;   // 2 per slot

@@ -401,3 +401,43 @@ def test_forward_and_transpose_overlap_on_two_streams(gm, name, prec):
     for od, om in outs:
         assert torch.equal(od, ref_d) and torch.equal(om, ref_m)
     op.close()
+
+
+def test_host_buffer_forward_and_transpose_from_two_threads(gm):
+    """With page-locked buffers the host-buffer forward and transpose of one handle may run from
+    two host threads at the same time (separate workspaces, no staging): bit for bit the serial
+    results."""
+    import threading
+
+    import torch
+
+    w = W.WORKLOADS["grav300"]
+    op = gm.Operator.from_workload(w, precision=gm.F32)
+    m = torch.as_tensor(W.model("grav300", 0), dtype=torch.float32).contiguous().pin_memory()
+    d = torch.as_tensor(W.data("grav300", 0), dtype=torch.float32).contiguous().pin_memory()
+    ref_d = op.forward(m.cuda()).cpu()
+    ref_m = op.transpose(d.cuda()).cpu()
+    od = [torch.empty(op.data_shape, dtype=torch.float32).pin_memory() for _ in range(3)]
+    om = [torch.empty(op.model_shape, dtype=torch.float32).pin_memory() for _ in range(3)]
+    sf, st = torch.cuda.Stream(), torch.cuda.Stream()
+    errors = []
+
+    def loop(fn, src, outs, stream):
+        try:
+            for o in outs:
+                fn(src, o, stream=stream)
+        except Exception as e:  # reported below: an exception in a thread would not fail the test
+            errors.append(e)
+
+    th = [threading.Thread(target=loop, args=(op.forward_host, m, od, sf)),
+          threading.Thread(target=loop, args=(op.transpose_host, d, om, st))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors, errors
+    for a in od:
+        assert torch.equal(a, ref_d)
+    for b in om:
+        assert torch.equal(b, ref_m)
+    op.close()
