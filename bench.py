@@ -52,6 +52,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--table1", action="store_true", help="run the Table 1 size sweep instead")
     ap.add_argument("--table1-k", default="1-12", help="sizes k of the sweep, e.g. 1-12 or 3,6,12")
+    ap.add_argument("--table1-stations", type=int, default=16,
+                    help="oracle stations sampled per size for the forward error (each is a full row of G)")
     return ap.parse_args(argv)
 
 
@@ -715,7 +717,7 @@ def run_table1(args):
         d_np = W.random_vector(w.data_shape, k)
         row = {"table1_k": k, "padding": pad, "stations": [w.sx, w.sy], "nz": w.nz, "cells": w.n}
         rng = np.random.default_rng(100 + k)
-        st = np.sort(rng.choice(w.m, size=min(64, w.m), replace=False))
+        st = np.sort(rng.choice(w.m, size=min(args.table1_stations, w.m), replace=False))
         ce = np.sort(rng.choice(w.n, size=64, replace=False))
         ref_f = O.forward(geom, m_np, stations=st)
         ref_t = O.transpose(geom, d_np, cells=ce)
