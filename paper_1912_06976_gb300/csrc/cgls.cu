@@ -7,7 +7,9 @@
 // product, Sec. 7) plus the vector updates below.  Scalars (gamma, delta, the
 // step lengths) live in device memory, dot products are accumulated in FP64
 // with a fixed two-stage reduction (bit-reproducible), and no iteration waits
-// for the host.
+// for the host.  The second stage of each reduction and the scalar update that
+// follows it run in the last block of the reduction kernel to arrive, so an
+// iteration takes four vector kernels besides the two products.
 //
 //   r = d - G x0;  s = G^T r - alpha^2 x0;  p = s;  gamma = ||s||^2
 //   repeat: q = G p;  delta = ||q||^2 + alpha^2 ||p||^2;  a = gamma / delta
@@ -30,8 +32,8 @@ namespace gm {
 constexpr int kRedBlocks = 512;
 constexpr int kRedThreads = 256;
 
-// scalar slots
-enum { S_GAMMA = 0, S_A = 1, S_B = 2, S_ALPHA2 = 3, S_THRESH = 4, S_DONE = 5, S_COUNT = 8 };
+// scalar slots (S_ARRIVE holds the arrival count of the reduction blocks, as an unsigned int)
+enum { S_GAMMA = 0, S_A = 1, S_B = 2, S_ALPHA2 = 3, S_THRESH = 4, S_DONE = 5, S_ARRIVE = 6, S_COUNT = 8 };
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -45,15 +47,37 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return v;
 }
 
-// part[blk] = partial SUM a[i]^2 (i < na); part[kRedBlocks + blk] = partial SUM b[i]^2 (i < nb)
-template <typename R>
-__global__ void k_sumsq2(const R *a, size_t na, const R *b, size_t nb, double *part) {
+// Partial sums written by other blocks of the same launch, read through L2 (not L1).
+__device__ double sum_parts(const double *part, double *sh) {
+    double v = 0;
+    for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) v += __ldcg(part + i);
+    return block_sum(v, sh);
+}
+
+// The reductions of an iteration with their scalar step fused in: every block reduces its share
+// of SUM a^2 and SUM b^2 into part[], and the last block to arrive (an atomic count; nothing
+// waits) sums the parts in block order and updates the scalars.  MODE
+//   0 step length:  a = q, b = p;  a_step = gamma / (||q||^2 + alpha^2 ||p||^2), 0 once converged
+//   1 beta:         a = s after s -= alpha^2 x, b = r;  beta = ||s||^2 / gamma, gamma = ||s||^2,
+//                   resid[k] = ||r||
+//   2 init:         a = s after s -= alpha^2 x and p = s, b = r;  gamma = ||s||^2, resid[0] = ||r||
+template <typename R, int MODE>
+__global__ void k_reduce_step(R *a, size_t na, const R *b, size_t nb, const R *x, R *pv, R a2, double *part,
+                              double *sc, double *resid, int k, double alpha2, double tol2) {
     pdl_wait();
     pdl_trigger();
     __shared__ double sh[32];
+    __shared__ unsigned int s_last;
     double sa = 0, sb = 0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < na; i += (size_t)gridDim.x * blockDim.x)
-        sa += (double)a[i] * (double)a[i];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < na; i += (size_t)gridDim.x * blockDim.x) {
+        R v = a[i];
+        if (MODE != 0) {
+            v = v - a2 * x[i];
+            a[i] = v;
+            if (MODE == 2) pv[i] = v;
+        }
+        sa += (double)v * (double)v;
+    }
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nb; i += (size_t)gridDim.x * blockDim.x)
         sb += (double)b[i] * (double)b[i];
     sa = block_sum(sa, sh);
@@ -62,57 +86,33 @@ __global__ void k_sumsq2(const R *a, size_t na, const R *b, size_t nb, double *p
         part[blockIdx.x] = sa;
         part[kRedBlocks + blockIdx.x] = sb;
     }
-}
-
-__device__ double sum_parts(const double *part, double *sh) {
-    double v = 0;
-    for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) v += part[i];
-    return block_sum(v, sh);
-}
-
-// init: gamma = ||s||^2 (parts[0..]); resid[0] = sqrt(||r||^2) (parts[K..]);
-// converged once gamma <= tol2 * gamma_0
-__global__ void k_init_scalars(const double *part, double *sc, double *resid, double alpha2, double tol2) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ double sh[32];
-    double s2 = sum_parts(part, sh);
-    double r2 = sum_parts(part + kRedBlocks, sh);
+    __threadfence();
+    __syncthreads();
+    unsigned int *arrive = reinterpret_cast<unsigned int *>(sc + S_ARRIVE);
+    if (threadIdx.x == 0) s_last = (atomicAdd(arrive, 1u) == gridDim.x - 1u) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const double A = sum_parts(part, sh);
+    const double B = sum_parts(part + kRedBlocks, sh);
     if (threadIdx.x == 0) {
-        sc[S_GAMMA] = s2;
-        sc[S_ALPHA2] = alpha2;
-        sc[S_THRESH] = tol2 * s2;
-        sc[S_DONE] = (s2 > 0) ? 0.0 : 1.0;
-        resid[0] = sqrt(r2);
-    }
-}
-
-// a = gamma / (||q||^2 + alpha^2 ||p||^2), or 0 once converged
-__global__ void k_step_length(const double *part, double *sc) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ double sh[32];
-    double q2 = sum_parts(part, sh);
-    double p2 = sum_parts(part + kRedBlocks, sh);
-    if (threadIdx.x == 0) {
-        if (sc[S_GAMMA] <= sc[S_THRESH]) sc[S_DONE] = 1.0;
-        double delta = q2 + sc[S_ALPHA2] * p2;
-        sc[S_A] = (sc[S_DONE] == 0.0 && delta > 0) ? sc[S_GAMMA] / delta : 0.0;
-    }
-}
-
-// b = gamma' / gamma (0 once converged), gamma = gamma'; resid[k] = ||r||
-__global__ void k_beta(const double *part, double *sc, double *resid, int k) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ double sh[32];
-    double s2 = sum_parts(part, sh);
-    double r2 = sum_parts(part + kRedBlocks, sh);
-    if (threadIdx.x == 0) {
-        double g = sc[S_GAMMA];
-        sc[S_B] = (sc[S_DONE] == 0.0 && g > 0) ? s2 / g : 0.0;
-        sc[S_GAMMA] = s2;
-        resid[k] = sqrt(r2);
+        *arrive = 0u;  // ready for the next reduction
+        if (MODE == 0) {
+            if (sc[S_GAMMA] <= sc[S_THRESH]) sc[S_DONE] = 1.0;
+            const double delta = A + sc[S_ALPHA2] * B;
+            sc[S_A] = (sc[S_DONE] == 0.0 && delta > 0) ? sc[S_GAMMA] / delta : 0.0;
+        } else if (MODE == 1) {
+            const double g = sc[S_GAMMA];
+            sc[S_B] = (sc[S_DONE] == 0.0 && g > 0) ? A / g : 0.0;
+            sc[S_GAMMA] = A;
+            resid[k] = sqrt(B);
+        } else {
+            sc[S_GAMMA] = A;
+            sc[S_ALPHA2] = alpha2;
+            sc[S_THRESH] = tol2 * A;
+            sc[S_DONE] = (A > 0) ? 0.0 : 1.0;
+            resid[0] = sqrt(B);
+        }
     }
 }
 
@@ -133,18 +133,6 @@ __global__ void k_residual0(const R *d, R *r, size_t m) {
     pdl_trigger();
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
         r[i] = d[i] - r[i];
-}
-
-// s -= alpha^2 x; p = s (when set_p)
-template <typename R>
-__global__ void k_s_update(R *s, const R *x, R *p, size_t n, R a2, int set_p) {
-    pdl_wait();
-    pdl_trigger();
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        R v = s[i] - a2 * x[i];
-        s[i] = v;
-        if (set_p) p[i] = v;
-    }
 }
 
 // x += a p (i < n); r -= a q (i < m)
@@ -202,6 +190,7 @@ static cudaError_t cgls_t(gm_plan *p, const R *d, const R *x0, R *x, double alph
         e = (x);                                   \
         if (e != cudaSuccess) goto out;            \
     } while (0)
+    CG_TRY(cudaMemsetAsync(sc, 0, sizeof(double) * S_COUNT, st));  // the arrival count starts at zero
     if (x0 && x0 != x) CG_TRY(cudaMemcpyAsync(x, x0, sizeof(R) * n, cudaMemcpyDeviceToDevice, st));
     if (!x0) CG_TRY(cudaMemsetAsync(x, 0, sizeof(R) * n, st));
     {
@@ -215,24 +204,22 @@ static cudaError_t cgls_t(gm_plan *p, const R *d, const R *x0, R *x, double alph
         CG_TRY(launch_transpose(p, r, s, st, &l));  // s = G^T r
         launches += l;
     }
-    launch_pdl(k_s_update<R>, dim3(vb), dim3(vt), 0, st, s, x, pv, n, (R)(alpha * alpha), 1);
-    launch_pdl(k_sumsq2<R>, dim3(vb), dim3(vt), 0, st, s, n, r, m, part);
-    launch_pdl(k_init_scalars, dim3(1), dim3(1024), 0, st, part, sc, resid, alpha * alpha, cgls_tol2(p->precision));
-    launches += 4;
+    launch_pdl(k_reduce_step<R, 2>, dim3(vb), dim3(vt), 0, st, s, n, (const R *)r, m, (const R *)x, pv,
+               (R)(alpha * alpha), part, sc, resid, 0, alpha * alpha, cgls_tol2(p->precision));
+    launches += 2;
     for (k = 1; k <= iters; ++k) {
         int l = 0;
         CG_TRY(launch_forward(p, pv, q, st, &l));  // q = G p
         launches += l;
-        launch_pdl(k_sumsq2<R>, dim3(vb), dim3(vt), 0, st, q, m, pv, n, part);
-        launch_pdl(k_step_length, dim3(1), dim3(1024), 0, st, part, sc);
+        launch_pdl(k_reduce_step<R, 0>, dim3(vb), dim3(vt), 0, st, q, m, (const R *)pv, n, (const R *)nullptr,
+                   (R *)nullptr, (R)0, part, sc, resid, k, 0.0, 0.0);
         launch_pdl(k_update_xr<R>, dim3(vb), dim3(vt), 0, st, x, pv, n, r, q, m, sc);
         CG_TRY(launch_transpose(p, r, s, st, &l));  // s = G^T r
         launches += l;
-        launch_pdl(k_s_update<R>, dim3(vb), dim3(vt), 0, st, s, x, pv, n, (R)(alpha * alpha), 0);
-        launch_pdl(k_sumsq2<R>, dim3(vb), dim3(vt), 0, st, s, n, r, m, part);
-        launch_pdl(k_beta, dim3(1), dim3(1024), 0, st, part, sc, resid, k);
+        launch_pdl(k_reduce_step<R, 1>, dim3(vb), dim3(vt), 0, st, s, n, (const R *)r, m, (const R *)x,
+                   (R *)nullptr, (R)(alpha * alpha), part, sc, resid, k, 0.0, 0.0);
         launch_pdl(k_update_p<R>, dim3(vb), dim3(vt), 0, st, pv, s, n, sc);
-        launches += 6;
+        launches += 4;
         CG_TRY(cudaGetLastError());
     }
     CG_TRY(cudaGetLastError());
@@ -322,24 +309,22 @@ static cudaError_t cgls_noalloc_t(gm_plan *p, const R *d, const R *x0, R *x, dou
         NA_TRY(launch_transpose(p, r, s, st, &l));
         launches += l;
     }
-    launch_pdl(k_s_update<R>, dim3(vb), dim3(vt), 0, st, s, x, pv, n, (R)(alpha * alpha), 1);
-    launch_pdl(k_sumsq2<R>, dim3(vb), dim3(vt), 0, st, s, n, r, m, part);
-    launch_pdl(k_init_scalars, dim3(1), dim3(1024), 0, st, part, sc, resid, alpha * alpha, cgls_tol2(p->precision));
-    launches += 4;
+    launch_pdl(k_reduce_step<R, 2>, dim3(vb), dim3(vt), 0, st, s, n, (const R *)r, m, (const R *)x, pv,
+               (R)(alpha * alpha), part, sc, resid, 0, alpha * alpha, cgls_tol2(p->precision));
+    launches += 2;
     for (k = 1; k <= iters; ++k) {
         int l = 0;
         NA_TRY(launch_forward(p, pv, q, st, &l));
         launches += l;
-        launch_pdl(k_sumsq2<R>, dim3(vb), dim3(vt), 0, st, q, m, pv, n, part);
-        launch_pdl(k_step_length, dim3(1), dim3(1024), 0, st, part, sc);
+        launch_pdl(k_reduce_step<R, 0>, dim3(vb), dim3(vt), 0, st, q, m, (const R *)pv, n, (const R *)nullptr,
+                   (R *)nullptr, (R)0, part, sc, resid, k, 0.0, 0.0);
         launch_pdl(k_update_xr<R>, dim3(vb), dim3(vt), 0, st, x, pv, n, r, q, m, sc);
         NA_TRY(launch_transpose(p, r, s, st, &l));
         launches += l;
-        launch_pdl(k_s_update<R>, dim3(vb), dim3(vt), 0, st, s, x, pv, n, (R)(alpha * alpha), 0);
-        launch_pdl(k_sumsq2<R>, dim3(vb), dim3(vt), 0, st, s, n, r, m, part);
-        launch_pdl(k_beta, dim3(1), dim3(1024), 0, st, part, sc, resid, k);
+        launch_pdl(k_reduce_step<R, 1>, dim3(vb), dim3(vt), 0, st, s, n, (const R *)r, m, (const R *)x,
+                   (R *)nullptr, (R)(alpha * alpha), part, sc, resid, k, 0.0, 0.0);
         launch_pdl(k_update_p<R>, dim3(vb), dim3(vt), 0, st, pv, s, n, sc);
-        launches += 6;
+        launches += 4;
         NA_TRY(cudaGetLastError());
     }
     NA_TRY(cudaGetLastError());

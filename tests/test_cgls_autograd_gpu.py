@@ -133,7 +133,8 @@ def test_cgls_mag128_inversion(gm):
     # the recursively updated FP32 residual drifts from the true one by O(iters * eps32 * ||d||)
     r = float((op64.forward(x.double()) - d).norm())
     assert abs(r - res[-1]) < 1e-4 * res[0], (r, res[-1], res[0])
-    # start-up: G x0, G^T r and 4 vector kernels; per iteration: G p, G^T r and 6 vector kernels
-    assert op32.last_launch_count() == n_fwd + n_tr + 4 + 50 * (n_fwd + n_tr + 6)
+    # start-up: G x0, G^T r and 2 vector kernels; per iteration: G p, G^T r and 4 vector kernels
+    # (the reductions finish their scalar step in the last block to arrive)
+    assert op32.last_launch_count() == n_fwd + n_tr + 2 + 50 * (n_fwd + n_tr + 4)
     op32.close()
     op64.close()
