@@ -30,15 +30,15 @@
  * Ownership: the handle owns the spectra, the FFT twiddle tables and its
  * workspace, all allocated by the setup call on the device that is current
  * then; the caller owns every m / d buffer it passes.  Applies allocate
- * nothing, do not synchronise (except the *_host variants) and are ordered on
- * the CUDA stream passed in (NULL = the legacy default stream).  The forward
- * and the transpose products of a handle have separate workspaces: one
- * forward and one transpose (apply_forward / apply_transpose, or their
- * host-buffer variants with page-locked buffers, e.g. from two host threads)
- * may run at the same time on two streams (independent products, e.g. G m and
- * G^T d of one step).  Other calls on one handle must not overlap in time: two
- * forwards, two transposes, host-buffer variants with pageable buffers (one
- * staging area), gm_cgls / gm_cgls_noalloc (which use both products), and any
+ * nothing, do not synchronise (except apply_forward_host /
+ * apply_transpose_host) and are ordered on the CUDA stream passed in (NULL =
+ * the legacy default stream).  The forward and the transpose products of a
+ * handle have separate workspaces and host-call staging buffers: one forward
+ * and one transpose (apply_forward / apply_transpose, or any of their
+ * host-buffer variants, e.g. from two host threads) may run at the same time
+ * on two streams (independent products, e.g. G m and G^T d of one step).
+ * Other calls on one handle must not overlap in time: two forwards, two
+ * transposes, gm_cgls / gm_cgls_noalloc (which use both products), and any
  * call while per-kernel timing is enabled; serialise them on one stream.
  * Distinct handles are independent.
  *
@@ -133,15 +133,30 @@ GM_API gm_status apply_forward(gm_handle h, const void *m_dev, void *d_dev, void
  * generator is real).  d_dev: m elements, m_dev: n elements, overwritten. */
 GM_API gm_status apply_transpose(gm_handle h, const void *d_dev, void *m_dev, void *stream);
 
-/* The same products from and to HOST buffers; they synchronise the stream
- * before returning.  When both buffers are page-locked (cudaHostAlloc /
- * cudaHostRegister, e.g. torch pin_memory) the kernels read the input and
- * write the output in place through the GPU's view of host memory, with no
- * copies; otherwise (or with GM_HOST_STAGING=1 in the environment) the input
- * is copied to the handle's device staging buffer, the product runs there and
- * the result is copied back.  Pageable memory works in the staged form. */
+/* The same products from and to HOST buffers (m_host: n elements, d_host: m
+ * elements, in the handle's precision; the two must not overlap, GM_EINVAL).
+ * The input is copied by the copy engine to the direction's device staging
+ * buffer, the product runs there and the result is copied back, all on
+ * `stream`; these two calls synchronise the stream before returning.
+ * Page-locked buffers (cudaHostAlloc / cudaHostRegister, e.g. torch
+ * pin_memory) give the full host-link rate; pageable memory works too.  With
+ * GM_HOST_DIRECT=1 in the environment and both buffers page-locked, the
+ * kernels instead read the input and write the output in place through the
+ * GPU's view of host memory (no staging copies). */
 GM_API gm_status apply_forward_host(gm_handle h, const void *m_host, void *d_host, void *stream);
 GM_API gm_status apply_transpose_host(gm_handle h, const void *d_host, void *m_host, void *stream);
+
+/* Stream-ordered forms of the two calls above: they enqueue the copies and the
+ * product on `stream` and return without waiting.  The output is complete, and
+ * the input may be changed, once the stream has reached the point of the call
+ * (cudaStreamSynchronize, an event); until then both host buffers must stay
+ * allocated.  With page-locked buffers the call returns at once, so successive
+ * products overlap their host-link transfers with each other's kernels; with
+ * pageable buffers the copies block the calling thread as cudaMemcpyAsync
+ * does.  Successive calls of one direction reuse its staging buffer: issue
+ * them on one stream (or order them), like apply_forward / apply_transpose. */
+GM_API gm_status apply_forward_host_async(gm_handle h, const void *m_host, void *d_host, void *stream);
+GM_API gm_status apply_transpose_host_async(gm_handle h, const void *d_host, void *m_host, void *stream);
 
 /* Releases everything the handle owns (synchronises its device first).
  * NULL is accepted and returns GM_OK. */

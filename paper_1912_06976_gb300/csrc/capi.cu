@@ -143,6 +143,8 @@ static void free_plan(gm_plan *p) {
     cudaFree(p->work_counters);
     cudaFree(p->stage_m);
     cudaFree(p->stage_d);
+    cudaFree(p->stage_m_tr);
+    cudaFree(p->stage_d_tr);
     cudaFree(p->tw_x);
     cudaFree(p->tw_y);
     cudaFree(p->cgls_buf);
@@ -304,7 +306,7 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
         part = cel * (size_t)p->fast_groups_fwd * g.Kx * g.NPy;
         ncount = (size_t)gm::fast_column_groups(p);
     }
-    p->work_bytes = 2 * (big + small) + part + rel * (n_model + n_data);
+    p->work_bytes = 2 * (big + small) + part + 2 * rel * (n_model + n_data);
     const size_t setup_peak = sizeof(double) * ((size_t)(p->Nx + 1) * (p->Ny + 1) * g.nz +
                                                 (size_t)g.NPx * g.NPy * g.nz) +
                               sizeof(double2) * nspec + 4 * sizeof(double2) * (g.NPx + g.NPy);
@@ -348,6 +350,8 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
     }
     SETUP_TRY(cudaMalloc(&p->stage_m, rel * n_model), "staging");
     SETUP_TRY(cudaMalloc(&p->stage_d, rel * n_data), "staging");
+    SETUP_TRY(cudaMalloc(&p->stage_m_tr, rel * n_model), "staging");
+    SETUP_TRY(cudaMalloc(&p->stage_d_tr, rel * n_data), "staging");
     cudaStream_t s;
     SETUP_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
     cudaError_t be = gm::build_spectra(p, s);
@@ -428,48 +432,62 @@ static void *device_view_of_pinned(const void *p) {
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
-static gm_status host_apply(gm_handle h, const void *in_host, void *out_host, void *stream, bool fwd) {
+static gm_status host_apply(gm_handle h, const void *in_host, void *out_host, void *stream, bool fwd, bool sync) {
     if (!h) return fail(GM_EINVAL, "handle is NULL");
     if (!in_host || !out_host) return fail(GM_EINVAL, "NULL buffer");
-    DeviceGuard dg(h->device);
     const size_t rel = h->precision == GM_F32 ? sizeof(float) : sizeof(double);
     const size_t n = (size_t)h->geo.nx * h->geo.ny * h->geo.nz, m = (size_t)h->geo.sx * h->geo.sy;
+    const size_t nin = fwd ? n : m, nout = fwd ? m : n;
+    if (overlaps(in_host, nin * rel, out_host, nout * rel)) return fail(GM_EINVAL, "input and output overlap");
+    DeviceGuard dg(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // Page-locked buffers are read and written in place by the kernels (over the host link), with
-    // no staging copies; GM_HOST_STAGING=1 forces the staged path.
-    const char *stg = std::getenv("GM_HOST_STAGING");
-    void *in_dev = device_view_of_pinned(in_host), *out_dev = device_view_of_pinned(out_host);
-    if (in_dev && out_dev && !(stg && stg[0] && stg[0] != '0')) {
-        int nl = 0;
-        cudaError_t e = fwd ? gm::launch_forward(h, in_dev, out_dev, s, &nl)
-                            : gm::launch_transpose(h, in_dev, out_dev, s, &nl);
+    int nl = 0;
+    cudaError_t e = cudaSuccess;
+    // Default: the copy engines move the input into the direction's staging buffer and the result
+    // out of it, so the SMs run the product on device memory while the host link is busy.  With
+    // GM_HOST_DIRECT=1 and page-locked buffers the kernels read and write the host buffers in
+    // place through the GPU's view of host memory instead.
+    const char *direct = std::getenv("GM_HOST_DIRECT");
+    void *in_dev = nullptr, *out_dev = nullptr;
+    if (direct && direct[0] && direct[0] != '0') {
+        in_dev = device_view_of_pinned(in_host);
+        out_dev = device_view_of_pinned(out_host);
+    }
+    if (in_dev && out_dev) {
+        e = fwd ? gm::launch_forward(h, in_dev, out_dev, s, &nl) : gm::launch_transpose(h, in_dev, out_dev, s, &nl);
         h->last_launches = nl;
         if (e != cudaSuccess) return cuda_fail(e, "apply");
+    } else {
+        void *din = fwd ? h->stage_m : h->stage_d_tr, *dout = fwd ? h->stage_d : h->stage_m_tr;
+        e = cudaMemcpyAsync(din, in_host, rel * nin, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+        e = fwd ? gm::launch_forward(h, din, dout, s, &nl) : gm::launch_transpose(h, din, dout, s, &nl);
+        h->last_launches = nl;
+        if (e != cudaSuccess) return cuda_fail(e, "apply");
+        e = cudaMemcpyAsync(out_host, dout, rel * nout, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    }
+    if (sync) {
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "synchronise");
-        return ok();
     }
-    void *din = fwd ? h->stage_m : h->stage_d, *dout = fwd ? h->stage_d : h->stage_m;
-    const size_t nin = fwd ? n : m, nout = fwd ? m : n;
-    cudaError_t e = cudaMemcpyAsync(din, in_host, rel * nin, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
-    int nl = 0;
-    e = fwd ? gm::launch_forward(h, din, dout, s, &nl) : gm::launch_transpose(h, din, dout, s, &nl);
-    h->last_launches = nl;
-    if (e != cudaSuccess) return cuda_fail(e, "apply");
-    e = cudaMemcpyAsync(out_host, dout, rel * nout, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e, "synchronise");
     return ok();
 }
 
 gm_status apply_forward_host(gm_handle h, const void *m_host, void *d_host, void *stream) {
-    return host_apply(h, m_host, d_host, stream, true);
+    return host_apply(h, m_host, d_host, stream, true, true);
 }
 
 gm_status apply_transpose_host(gm_handle h, const void *d_host, void *m_host, void *stream) {
-    return host_apply(h, d_host, m_host, stream, false);
+    return host_apply(h, d_host, m_host, stream, false, true);
+}
+
+gm_status apply_forward_host_async(gm_handle h, const void *m_host, void *d_host, void *stream) {
+    return host_apply(h, m_host, d_host, stream, true, false);
+}
+
+gm_status apply_transpose_host_async(gm_handle h, const void *d_host, void *m_host, void *stream) {
+    return host_apply(h, d_host, m_host, stream, false, false);
 }
 
 gm_status grav_mag_destroy(gm_handle h) {

@@ -33,12 +33,13 @@ struct gm_plan {
     bool spec_real = false;
 
     // Workspace: the large intermediate (forward [Kx][nz][ny], transpose [nz][ny][Kx]),
-    // the small one (forward [sy][Kx], transpose [Kx][sy]) and host-call staging.  The forward
-    // and the transpose each have their own pair, so that one of each may run at the same time
-    // on different streams.
+    // the small one (forward [sy][Kx], transpose [Kx][sy]) and host-call staging (a model and a
+    // data vector).  The forward and the transpose each have their own set, so that one of each
+    // may run at the same time on different streams.
     void *work_big = nullptr, *work_small = nullptr;        // forward
     void *work_big_tr = nullptr, *work_small_tr = nullptr;  // transpose
-    void *stage_m = nullptr, *stage_d = nullptr;
+    void *stage_m = nullptr, *stage_d = nullptr;            // forward host calls
+    void *stage_m_tr = nullptr, *stage_d_tr = nullptr;      // transpose host calls
     size_t work_bytes = 0;
 
     // Register-codelet path (apply_fast.cu): used when both FFT lengths have instantiations.
@@ -69,17 +70,27 @@ enum KernelId {
 };
 extern const char *const kKernelNames[K_COUNT];
 
+// Records an event on s: inside a stream capture as an event-record node of the graph (the
+// external flag), otherwise as a plain record (the flag is refused outside a capture).
+inline void timing_record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusNone;
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, s);
+}
+
 // Records the "before" event of a timed launch; returns the slot or -1.
 inline int timing_begin(gm_plan *p, cudaStream_t s, int kid) {
     if (p->tused >= (int)p->tkid.size()) return -1;
     int slot = p->tused++;
     p->tkid[slot] = kid;
-    // external: inside a stream capture the record becomes an event-record node of the graph
-    cudaEventRecordWithFlags(p->tev[2 * slot], s, cudaEventRecordExternal);
+    timing_record(p->tev[2 * slot], s);
     return slot;
 }
 inline void timing_end(gm_plan *p, cudaStream_t s, int slot) {
-    if (slot >= 0) cudaEventRecordWithFlags(p->tev[2 * slot + 1], s, cudaEventRecordExternal);
+    if (slot >= 0) timing_record(p->tev[2 * slot + 1], s);
 }
 }  // namespace gm
 

@@ -97,6 +97,8 @@ def load():
             "apply_transpose": (c_int, [vp, vp, vp, vp]),
             "apply_forward_host": (c_int, [vp, vp, vp, vp]),
             "apply_transpose_host": (c_int, [vp, vp, vp, vp]),
+            "apply_forward_host_async": (c_int, [vp, vp, vp, vp]),
+            "apply_transpose_host_async": (c_int, [vp, vp, vp, vp]),
             "grav_mag_destroy": (c_int, [vp]),
             "gm_get_info": (c_int, [vp, ctypes.POINTER(Info)]),
             "gm_copy_spectrum": (c_int, [vp, vp, c_size_t]),
@@ -260,8 +262,22 @@ class Operator:
         return out_host
 
     def transpose_host(self, d_host, out_host, stream=None):
+        """m' = G^T d with host tensors (copies inside; synchronises)."""
         _check(load().apply_transpose_host(self._h, self._host_arg(d_host, self.info.n_data),
                                            self._host_arg(out_host, self.info.n_model), _stream_ptr(stream)))
+        return out_host
+
+    def forward_host_async(self, m_host, out_host, stream=None):
+        """d = G m with host tensors, enqueued on `stream` without waiting: out_host is complete
+        once the stream has been synchronised; both tensors must stay alive until then."""
+        _check(load().apply_forward_host_async(self._h, self._host_arg(m_host, self.info.n_model),
+                                               self._host_arg(out_host, self.info.n_data), _stream_ptr(stream)))
+        return out_host
+
+    def transpose_host_async(self, d_host, out_host, stream=None):
+        """m' = G^T d with host tensors, enqueued on `stream` without waiting (see forward_host_async)."""
+        _check(load().apply_transpose_host_async(self._h, self._host_arg(d_host, self.info.n_data),
+                                                 self._host_arg(out_host, self.info.n_model), _stream_ptr(stream)))
         return out_host
 
     def spectrum(self) -> np.ndarray:

@@ -312,8 +312,9 @@ def test_asymmetric_padding_and_magnetic_keep_complex_spectra(gm):
 
 @pytest.mark.parametrize("prec", [1, 0, 2])
 def test_host_entry_points_direct_and_staged_agree(gm, monkeypatch, prec):
-    """Pinned buffers are used in place by the kernels; GM_HOST_STAGING=1 stages them through
-    device memory; pageable buffers are always staged.  All three give the device result."""
+    """Host buffers are staged through device memory by the copy engines; with GM_HOST_DIRECT=1
+    pinned buffers are used in place by the kernels; pageable buffers are always staged.  All
+    three give the device result."""
     import torch
 
     w = W.WORKLOADS["grav300"]
@@ -324,11 +325,11 @@ def test_host_entry_points_direct_and_staged_agree(gm, monkeypatch, prec):
     ref_d = op.forward(m.cuda()).cpu()
     ref_m = op.transpose(d.cuda()).cpu()
     outs = []
-    for pinned, staged in ((True, False), (True, True), (False, False)):
+    for pinned, staged in ((True, False), (True, True), (False, True)):
         if staged:
-            monkeypatch.setenv("GM_HOST_STAGING", "1")
+            monkeypatch.delenv("GM_HOST_DIRECT", raising=False)
         else:
-            monkeypatch.delenv("GM_HOST_STAGING", raising=False)
+            monkeypatch.setenv("GM_HOST_DIRECT", "1")
         mi, di = (m.pin_memory(), d.pin_memory()) if pinned else (m.clone(), d.clone())
         od = torch.empty(op.data_shape, dtype=dt)
         om = torch.empty(op.model_shape, dtype=dt)
@@ -337,6 +338,72 @@ def test_host_entry_points_direct_and_staged_agree(gm, monkeypatch, prec):
         op.forward_host(mi, od)
         op.transpose_host(di, om)
         assert torch.equal(od, ref_d) and torch.equal(om, ref_m), (pinned, staged)
+    op.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_stream_ordered_host_calls_pipeline_on_two_streams(gm, pinned):
+    """The stream-ordered host-buffer calls: several steps of a forward (stream 1) and a
+    transpose (stream 2) enqueued without waiting, one synchronisation at the end; every step's
+    output is bit for bit the device result (same kernels, same inputs)."""
+    import torch
+
+    w = W.WORKLOADS["grav300"]
+    op = gm.Operator.from_workload(w, precision=gm.F32)
+    m = torch.as_tensor(W.model("grav300", 0), dtype=torch.float32).contiguous()
+    d = torch.as_tensor(W.data("grav300", 0), dtype=torch.float32).contiguous()
+    ref_d = op.forward(m.cuda()).cpu()
+    ref_m = op.transpose(d.cuda()).cpu()
+    pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
+    mi, di = pin(m.clone()), pin(d.clone())
+    od = [pin(torch.full(op.data_shape, float("nan"))) for _ in range(4)]
+    om = [pin(torch.full(op.model_shape, float("nan"))) for _ in range(4)]
+    sf, st = torch.cuda.Stream(), torch.cuda.Stream()
+    for a, b in zip(od, om):
+        op.forward_host_async(mi, a, stream=sf)
+        op.transpose_host_async(di, b, stream=st)
+    sf.synchronize()
+    st.synchronize()
+    for a, b in zip(od, om):
+        assert torch.equal(a, ref_d) and torch.equal(b, ref_m)
+    op.close()
+
+
+def test_host_calls_reject_overlapping_buffers(gm):
+    import torch
+
+    w = W.WORKLOADS["grav16"]
+    op = gm.Operator.from_workload(w, precision=gm.F32)
+    buf = torch.zeros(op.info.n_model + op.info.n_data, dtype=torch.float32).pin_memory()
+    m = buf[: op.info.n_model]
+    d_overlap = buf[op.info.n_model - op.info.n_data // 2:][: op.info.n_data]
+    for fn in (op.forward_host, op.forward_host_async):
+        with pytest.raises(gm.GravMagError) as ei:
+            fn(m, d_overlap)
+        assert ei.value.status == gm.GM_EINVAL
+    op.close()
+
+
+def test_per_kernel_timing_outside_graph_capture(gm):
+    """Per-kernel timing of eager calls (device and host-buffer entry points): one record per
+    launch, positive device times."""
+    import torch
+
+    w = W.WORKLOADS["grav300"]
+    op = gm.Operator.from_workload(w, precision=gm.F32)
+    m = torch.as_tensor(W.model("grav300", 0), dtype=torch.float32).contiguous()
+    d = torch.as_tensor(W.data("grav300", 0), dtype=torch.float32).contiguous()
+    ref_d = op.forward(m.cuda())
+    op.enable_timing(64)
+    got = op.forward(m.cuda())
+    n_fwd = op.last_launch_count()
+    kt = op.kernel_times()
+    assert sum(v[0] for v in kt.values()) == n_fwd and all(v[1] > 0 for v in kt.values()), kt
+    op.transpose_host(d.pin_memory(), torch.empty(op.model_shape).pin_memory())
+    kt = op.kernel_times()
+    assert sum(v[0] for v in kt.values()) == op.last_launch_count() and all(v[1] > 0 for v in kt.values()), kt
+    op.enable_timing(0)
+    assert torch.equal(got, ref_d)
     op.close()
 
 
