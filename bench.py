@@ -570,8 +570,9 @@ def run_ours(args):
     ts_max, _ = reduce_max_sum(t_e2e_serial, 2.0 * k_e2e)
     e2e = {"value": e_app / (te_max / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": 4 * (inf.n_model + inf.n_data), "d2h_bytes_per_step": 4 * (inf.n_data + inf.n_model),
-           "api": "apply_forward_host_async + apply_transpose_host_async (pinned host buffers, copy engines "
-                  "in and out of device staging), forward and transpose on two streams, one host thread, "
+           "api": "apply_forward_host_async + apply_transpose_host_async (pinned host buffers; the model "
+                  "vectors by the copy engines through double-buffered device staging, the data vectors "
+                  "in place by the kernels), forward and transpose on two streams, one host thread, "
                   "host clock from the first call to the synchronisation after the last",
            "steps": k_e2e,
            "sync_two_threads_value": e_app / (tt_max / 1e3),

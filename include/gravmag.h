@@ -135,26 +135,32 @@ GM_API gm_status apply_transpose(gm_handle h, const void *d_dev, void *m_dev, vo
 
 /* The same products from and to HOST buffers (m_host: n elements, d_host: m
  * elements, in the handle's precision; the two must not overlap, GM_EINVAL).
- * The input is copied by the copy engine to the direction's device staging
- * buffer, the product runs there and the result is copied back, all on
- * `stream`; these two calls synchronise the stream before returning.
- * Page-locked buffers (cudaHostAlloc / cudaHostRegister, e.g. torch
- * pin_memory) give the full host-link rate; pageable memory works too.  With
- * GM_HOST_DIRECT=1 in the environment and both buffers page-locked, the
- * kernels instead read the input and write the output in place through the
- * GPU's view of host memory (no staging copies). */
+ * Each direction has two model-sized device staging buffers used in turn, a
+ * data-sized one, and two internal streams: the model goes over the host link
+ * by the copy engine on one of them while the product runs on the other, so a
+ * call's model copy overlaps the kernels of the calls next to it.  `stream`
+ * waits for the call's last copy: the output is complete once `stream` has
+ * reached the end of the call.  These two calls also synchronise `stream`
+ * before returning.  Page-locked buffers (cudaHostAlloc / cudaHostRegister,
+ * e.g. torch pin_memory) give the full host-link rate; pageable memory works
+ * too.  With GM_HOST_DIRECT=1 in the environment and both buffers
+ * page-locked, the kernels instead read the input and write the output in
+ * place through the GPU's view of host memory, on `stream`. */
 GM_API gm_status apply_forward_host(gm_handle h, const void *m_host, void *d_host, void *stream);
 GM_API gm_status apply_transpose_host(gm_handle h, const void *d_host, void *m_host, void *stream);
 
-/* Stream-ordered forms of the two calls above: they enqueue the copies and the
- * product on `stream` and return without waiting.  The output is complete, and
- * the input may be changed, once the stream has reached the point of the call
- * (cudaStreamSynchronize, an event); until then both host buffers must stay
- * allocated.  With page-locked buffers the call returns at once, so successive
- * products overlap their host-link transfers with each other's kernels; with
- * pageable buffers the copies block the calling thread as cudaMemcpyAsync
- * does.  Successive calls of one direction reuse its staging buffer: issue
- * them on one stream (or order them), like apply_forward / apply_transpose. */
+/* The same calls without the final synchronisation: they enqueue the work and
+ * return.  The output is complete once `stream` has reached the end of the
+ * call (cudaStreamSynchronize, an event); until then both host buffers must
+ * stay allocated and the input unchanged.  Unlike apply_forward, the call may
+ * read the input and write the output before `stream` reaches it (the
+ * internal streams run ahead while consecutive calls of one direction come on
+ * one stream), so earlier work on `stream` must not write the input or use
+ * the output buffer.  Inside a stream capture the copies and the product are
+ * captured on `stream` in order.  With page-locked buffers the call returns at
+ * once; with pageable buffers the copies block the calling thread as
+ * cudaMemcpyAsync does.  Calls of one direction must be ordered (one stream,
+ * or events), like apply_forward / apply_transpose. */
 GM_API gm_status apply_forward_host_async(gm_handle h, const void *m_host, void *d_host, void *stream);
 GM_API gm_status apply_transpose_host_async(gm_handle h, const void *d_host, void *m_host, void *stream);
 

@@ -141,10 +141,15 @@ static void free_plan(gm_plan *p) {
     cudaFree(p->work_small_tr);
     cudaFree(p->work_part);
     cudaFree(p->work_counters);
-    cudaFree(p->stage_m);
-    cudaFree(p->stage_d);
-    cudaFree(p->stage_m_tr);
-    cudaFree(p->stage_d_tr);
+    for (gm_plan::HostPipe *hp : {&p->host_fwd, &p->host_tr}) {
+        cudaFree(hp->stage[0]);
+        cudaFree(hp->stage[1]);
+        cudaFree(hp->stage_small);
+        if (hp->ks) cudaStreamDestroy(hp->ks);
+        if (hp->cs) cudaStreamDestroy(hp->cs);
+        for (cudaEvent_t e : {hp->fork, hp->done, hp->ready[0], hp->ready[1], hp->freed[0], hp->freed[1]})
+            if (e) cudaEventDestroy(e);
+    }
     cudaFree(p->tw_x);
     cudaFree(p->tw_y);
     cudaFree(p->cgls_buf);
@@ -306,7 +311,7 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
         part = cel * (size_t)p->fast_groups_fwd * g.Kx * g.NPy;
         ncount = (size_t)gm::fast_column_groups(p);
     }
-    p->work_bytes = 2 * (big + small) + part + 2 * rel * (n_model + n_data);
+    p->work_bytes = 2 * (big + small) + part + 2 * rel * (2 * n_model + n_data);
     const size_t setup_peak = sizeof(double) * ((size_t)(p->Nx + 1) * (p->Ny + 1) * g.nz +
                                                 (size_t)g.NPx * g.NPy * g.nz) +
                               sizeof(double2) * nspec + 4 * sizeof(double2) * (g.NPx + g.NPy);
@@ -348,10 +353,15 @@ gm_handle grav_mag_setup_ex(const gm_params *prm) {
         // the memset is ordered on the legacy default stream only; applies may come on any stream
         SETUP_TRY(cudaDeviceSynchronize(), "workspace");
     }
-    SETUP_TRY(cudaMalloc(&p->stage_m, rel * n_model), "staging");
-    SETUP_TRY(cudaMalloc(&p->stage_d, rel * n_data), "staging");
-    SETUP_TRY(cudaMalloc(&p->stage_m_tr, rel * n_model), "staging");
-    SETUP_TRY(cudaMalloc(&p->stage_d_tr, rel * n_data), "staging");
+    for (gm_plan::HostPipe *hp : {&p->host_fwd, &p->host_tr}) {
+        SETUP_TRY(cudaMalloc(&hp->stage[0], rel * n_model), "staging");
+        SETUP_TRY(cudaMalloc(&hp->stage[1], rel * n_model), "staging");
+        SETUP_TRY(cudaMalloc(&hp->stage_small, rel * n_data), "staging");
+        SETUP_TRY(cudaStreamCreateWithFlags(&hp->ks, cudaStreamNonBlocking), "stream");
+        SETUP_TRY(cudaStreamCreateWithFlags(&hp->cs, cudaStreamNonBlocking), "stream");
+        for (cudaEvent_t *e : {&hp->fork, &hp->done, &hp->ready[0], &hp->ready[1], &hp->freed[0], &hp->freed[1]})
+            SETUP_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "event");
+    }
     cudaStream_t s;
     SETUP_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
     cudaError_t be = gm::build_spectra(p, s);
@@ -402,6 +412,7 @@ gm_status apply_forward(gm_handle h, const void *m_dev, void *d_dev, void *strea
     gm_status st = check_apply(h, m_dev, n, d_dev, m);
     if (st != GM_OK) return st;
     DeviceGuard dg(h->device);
+    h->host_fwd.chained = false;  // the next host-buffer forward waits for this one's stream
     int nl = 0;
     cudaError_t e = gm::launch_forward(h, m_dev, d_dev, static_cast<cudaStream_t>(stream), &nl);
     h->last_launches = nl;
@@ -415,6 +426,7 @@ gm_status apply_transpose(gm_handle h, const void *d_dev, void *m_dev, void *str
     gm_status st = check_apply(h, d_dev, m, m_dev, n);
     if (st != GM_OK) return st;
     DeviceGuard dg(h->device);
+    h->host_tr.chained = false;
     int nl = 0;
     cudaError_t e = gm::launch_transpose(h, d_dev, m_dev, static_cast<cudaStream_t>(stream), &nl);
     h->last_launches = nl;
@@ -432,6 +444,16 @@ static void *device_view_of_pinned(const void *p) {
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
+// One host-buffer product.  Page-locked buffers with GM_HOST_DIRECT=1: the kernels use them in
+// place on `stream`.  Inside a stream capture: copy in, product and copy out on `stream`, through
+// the direction's first staging buffer.  Otherwise the direction's pipeline: the model copy runs on
+// the copy stream (forward: in, into the staging buffer of this call; transpose: out, from it), the
+// product on the kernel stream (which also reads or writes the data vector, in place when it is
+// page-locked, else through the small staging buffer), and `stream` waits for the call's end.  The
+// two staging buffers alternate, so the model copy of one call overlaps the kernels of the next.
+// The internal streams wait for `stream` to reach the call unless the previous call of this
+// direction came on the same stream with nothing of this direction in between (it already made
+// `stream` wait for it, and the kernel stream keeps the calls in order).
 static gm_status host_apply(gm_handle h, const void *in_host, void *out_host, void *stream, bool fwd, bool sync) {
     if (!h) return fail(GM_EINVAL, "handle is NULL");
     if (!in_host || !out_host) return fail(GM_EINVAL, "NULL buffer");
@@ -441,36 +463,81 @@ static gm_status host_apply(gm_handle h, const void *in_host, void *out_host, vo
     if (overlaps(in_host, nin * rel, out_host, nout * rel)) return fail(GM_EINVAL, "input and output overlap");
     DeviceGuard dg(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    gm_plan::HostPipe &hp = fwd ? h->host_fwd : h->host_tr;
     int nl = 0;
     cudaError_t e = cudaSuccess;
-    // Default: the copy engines move the input into the direction's staging buffer and the result
-    // out of it, so the SMs run the product on device memory while the host link is busy.  With
-    // GM_HOST_DIRECT=1 and page-locked buffers the kernels read and write the host buffers in
-    // place through the GPU's view of host memory instead.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "stream query");
     const char *direct = std::getenv("GM_HOST_DIRECT");
     void *in_dev = nullptr, *out_dev = nullptr;
     if (direct && direct[0] && direct[0] != '0') {
         in_dev = device_view_of_pinned(in_host);
         out_dev = device_view_of_pinned(out_host);
     }
+    const bool chained = hp.chained && hp.chain == s;
+    hp.chained = false;  // set again below once this call has been enqueued in full
+#define HP_TRY(x, what)                                 \
+    do {                                                \
+        e = (x);                                        \
+        if (e != cudaSuccess) return cuda_fail(e, what); \
+    } while (0)
     if (in_dev && out_dev) {
-        e = fwd ? gm::launch_forward(h, in_dev, out_dev, s, &nl) : gm::launch_transpose(h, in_dev, out_dev, s, &nl);
-        h->last_launches = nl;
-        if (e != cudaSuccess) return cuda_fail(e, "apply");
+        HP_TRY(fwd ? gm::launch_forward(h, in_dev, out_dev, s, &nl) : gm::launch_transpose(h, in_dev, out_dev, s, &nl),
+               "apply");
+    } else if (cap != cudaStreamCaptureStatusNone) {
+        void *big = hp.stage[0], *small = hp.stage_small;
+        HP_TRY(cudaMemcpyAsync(fwd ? big : small, in_host, rel * nin, cudaMemcpyHostToDevice, s), "host-to-device copy");
+        HP_TRY(fwd ? gm::launch_forward(h, big, small, s, &nl) : gm::launch_transpose(h, small, big, s, &nl), "apply");
+        HP_TRY(cudaMemcpyAsync(out_host, fwd ? small : big, rel * nout, cudaMemcpyDeviceToHost, s),
+               "device-to-host copy");
     } else {
-        void *din = fwd ? h->stage_m : h->stage_d_tr, *dout = fwd ? h->stage_d : h->stage_m_tr;
-        e = cudaMemcpyAsync(din, in_host, rel * nin, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
-        e = fwd ? gm::launch_forward(h, din, dout, s, &nl) : gm::launch_transpose(h, din, dout, s, &nl);
-        h->last_launches = nl;
-        if (e != cudaSuccess) return cuda_fail(e, "apply");
-        e = cudaMemcpyAsync(out_host, dout, rel * nout, cudaMemcpyDeviceToHost, s);
-        if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+        const int b = hp.next;
+        if (!chained) {
+            HP_TRY(cudaEventRecord(hp.fork, s), "event record");
+            HP_TRY(cudaStreamWaitEvent(hp.ks, hp.fork, 0), "stream wait");
+        }
+        // The data vector (m elements) is read or written in place by the kernels when its buffer
+        // is page-locked: a copy-engine transfer of it would queue behind the other direction's
+        // model copy on the same engine.
+        if (fwd) {
+            void *d_view = device_view_of_pinned(out_host);
+            // copy stream: model in, once the call two back has finished with this staging buffer
+            HP_TRY(cudaStreamWaitEvent(hp.cs, hp.freed[b], 0), "stream wait");
+            HP_TRY(cudaMemcpyAsync(hp.stage[b], in_host, rel * n, cudaMemcpyHostToDevice, hp.cs), "host-to-device copy");
+            HP_TRY(cudaEventRecord(hp.ready[b], hp.cs), "event record");
+            // kernel stream: product, data out
+            HP_TRY(cudaStreamWaitEvent(hp.ks, hp.ready[b], 0), "stream wait");
+            HP_TRY(gm::launch_forward(h, hp.stage[b], d_view ? d_view : hp.stage_small, hp.ks, &nl), "apply");
+            HP_TRY(cudaEventRecord(hp.freed[b], hp.ks), "event record");
+            if (!d_view)
+                HP_TRY(cudaMemcpyAsync(out_host, hp.stage_small, rel * m, cudaMemcpyDeviceToHost, hp.ks),
+                       "device-to-host copy");
+            HP_TRY(cudaEventRecord(hp.done, hp.ks), "event record");
+        } else {
+            const void *d_view = device_view_of_pinned(in_host);
+            // kernel stream: data in, product into this call's staging buffer
+            if (!d_view)
+                HP_TRY(cudaMemcpyAsync(hp.stage_small, in_host, rel * m, cudaMemcpyHostToDevice, hp.ks),
+                       "host-to-device copy");
+            HP_TRY(cudaStreamWaitEvent(hp.ks, hp.freed[b], 0), "stream wait");
+            HP_TRY(gm::launch_transpose(h, d_view ? d_view : hp.stage_small, hp.stage[b], hp.ks, &nl), "apply");
+            HP_TRY(cudaEventRecord(hp.ready[b], hp.ks), "event record");
+            // copy stream: model out
+            HP_TRY(cudaStreamWaitEvent(hp.cs, hp.ready[b], 0), "stream wait");
+            HP_TRY(cudaMemcpyAsync(out_host, hp.stage[b], rel * n, cudaMemcpyDeviceToHost, hp.cs),
+                   "device-to-host copy");
+            HP_TRY(cudaEventRecord(hp.freed[b], hp.cs), "event record");
+            HP_TRY(cudaEventRecord(hp.done, hp.cs), "event record");
+        }
+        HP_TRY(cudaStreamWaitEvent(s, hp.done, 0), "stream wait");
+        hp.next = b ^ 1;
+        hp.chain = s;
+        hp.chained = true;
     }
-    if (sync) {
-        e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return cuda_fail(e, "synchronise");
-    }
+    h->last_launches = nl;
+    if (sync) HP_TRY(cudaStreamSynchronize(s), "synchronise");
+#undef HP_TRY
     return ok();
 }
 
@@ -558,6 +625,7 @@ gm_status gm_cgls(gm_handle h, const void *d_dev, const void *x0_dev, void *x_de
     if (!d_dev || !x_dev) return fail(GM_EINVAL, "NULL buffer");
     if (iters < 0 || !(alpha >= 0) || !std::isfinite(alpha)) return fail(GM_EINVAL, "iters >= 0 and alpha >= 0 required");
     DeviceGuard dg(h->device);
+    h->host_fwd.chained = h->host_tr.chained = false;
     int nl = 0;
     cudaError_t e = gm::run_cgls(h, d_dev, x0_dev, x_dev, alpha, iters, resid_host,
                                  static_cast<cudaStream_t>(stream), &nl);
@@ -580,6 +648,7 @@ gm_status gm_cgls_noalloc(gm_handle h, const void *d_dev, const void *x0_dev, vo
         return fail(GM_EINVAL, "gm_cgls_noalloc needs %zu bytes of scratch for this grid and iteration count; "
                                "its fixed array holds %zu (use gm_cgls)", need, cap);
     DeviceGuard dg(h->device);
+    h->host_fwd.chained = h->host_tr.chained = false;
     int nl = 0;
     cudaError_t e = gm::run_cgls_noalloc(h, d_dev, x0_dev, x_dev, alpha, iters, resid_host,
                                          static_cast<cudaStream_t>(stream), &nl);

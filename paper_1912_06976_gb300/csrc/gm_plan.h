@@ -32,14 +32,27 @@ struct gm_plan {
     size_t spec_bytes = 0;
     bool spec_real = false;
 
-    // Workspace: the large intermediate (forward [Kx][nz][ny], transpose [nz][ny][Kx]),
-    // the small one (forward [sy][Kx], transpose [Kx][sy]) and host-call staging (a model and a
-    // data vector).  The forward and the transpose each have their own set, so that one of each
-    // may run at the same time on different streams.
+    // Workspace: the large intermediate (forward [Kx][nz][ny], transpose [nz][ny][Kx]) and the
+    // small one (forward [sy][Kx], transpose [Kx][sy]).  The forward and the transpose each have
+    // their own pair, so that one of each may run at the same time on different streams.
     void *work_big = nullptr, *work_small = nullptr;        // forward
     void *work_big_tr = nullptr, *work_small_tr = nullptr;  // transpose
-    void *stage_m = nullptr, *stage_d = nullptr;            // forward host calls
-    void *stage_m_tr = nullptr, *stage_d_tr = nullptr;      // transpose host calls
+
+    // Host-buffer calls of one direction (capi.cu): two model-sized staging buffers used in turn
+    // and a data-sized one, an internal stream for the product and one for the host-link copy of
+    // the model, and the events that order them.  While consecutive calls come on one caller
+    // stream with nothing else of this direction in between (chained), the internal streams run
+    // ahead of the caller's stream, so one call's model copy overlaps its neighbours' kernels.
+    struct HostPipe {
+        void *stage[2] = {nullptr, nullptr};
+        void *stage_small = nullptr;
+        cudaStream_t ks = nullptr, cs = nullptr;
+        cudaEvent_t fork = nullptr, done = nullptr, ready[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+        int next = 0;
+        cudaStream_t chain = nullptr;
+        bool chained = false;
+    };
+    HostPipe host_fwd, host_tr;
     size_t work_bytes = 0;
 
     // Register-codelet path (apply_fast.cu): used when both FFT lengths have instantiations.

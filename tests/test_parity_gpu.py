@@ -369,6 +369,76 @@ def test_stream_ordered_host_calls_pipeline_on_two_streams(gm, pinned):
     op.close()
 
 
+def test_stream_ordered_host_calls_mixed_with_device_calls(gm):
+    """Host-buffer calls chained on one stream, with device calls of both directions and a stream
+    switch in between (each of which makes the next host call wait for its stream): every output
+    equals the device result for its own input."""
+    import torch
+
+    w = W.WORKLOADS["mag64"]
+    op = gm.Operator.from_workload(w, precision=gm.F32)
+    ms = [torch.as_tensor(W.model("mag64", k), dtype=torch.float32).contiguous() for k in range(4)]
+    ds = [torch.as_tensor(W.data("mag64", k), dtype=torch.float32).contiguous() for k in range(4)]
+    ref_d = [op.forward(x.cuda()).cpu() for x in ms]
+    ref_m = [op.transpose(x.cuda()).cpu() for x in ds]
+    mh = [x.pin_memory() for x in ms]
+    dh = [x.pin_memory() for x in ds]
+    od = [torch.empty(op.data_shape).pin_memory() for _ in range(4)]
+    om = [torch.empty(op.model_shape).pin_memory() for _ in range(4)]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    dev_d = torch.empty(op.data_shape, device="cuda")
+    dev_m = torch.empty(op.model_shape, device="cuda")
+    m2, d2 = ms[2].cuda(), ds[2].cuda()
+    torch.cuda.synchronize()
+    op.forward_host_async(mh[0], od[0], stream=s1)
+    op.transpose_host_async(dh[0], om[0], stream=s1)
+    op.forward_host_async(mh[1], od[1], stream=s1)
+    op.transpose_host_async(dh[1], om[1], stream=s1)
+    op.forward(m2, out=dev_d, stream=s1)
+    op.transpose(d2, out=dev_m, stream=s1)
+    op.forward_host_async(mh[2], od[2], stream=s1)
+    op.transpose_host_async(dh[2], om[2], stream=s1)
+    s2.wait_stream(s1)
+    op.forward_host_async(mh[3], od[3], stream=s2)
+    op.transpose_host_async(dh[3], om[3], stream=s2)
+    s1.synchronize()
+    s2.synchronize()
+    for k in range(4):
+        assert torch.equal(od[k], ref_d[k]) and torch.equal(om[k], ref_m[k]), k
+    assert torch.equal(dev_d.cpu(), ref_d[2]) and torch.equal(dev_m.cpu(), ref_m[2])
+    op.close()
+
+
+def test_stream_ordered_host_calls_in_a_cuda_graph(gm):
+    """Captured on a stream, the host-buffer calls become copy and kernel nodes of the graph;
+    each replay copies the current host input and writes the host output."""
+    import torch
+
+    w = W.WORKLOADS["mag64"]
+    op = gm.Operator.from_workload(w, precision=gm.F32)
+    mh = torch.zeros(op.model_shape).pin_memory()
+    dh = torch.zeros(op.data_shape).pin_memory()
+    od = torch.empty(op.data_shape).pin_memory()
+    om = torch.empty(op.model_shape).pin_memory()
+    s = torch.cuda.Stream()
+    op.forward_host_async(mh, od, stream=s)  # first use outside the capture
+    op.transpose_host_async(dh, om, stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        op.forward_host_async(mh, od, stream=s)
+        op.transpose_host_async(dh, om, stream=s)
+    for k in range(2):
+        x = torch.as_tensor(W.model("mag64", k), dtype=torch.float32)
+        y = torch.as_tensor(W.data("mag64", k), dtype=torch.float32)
+        mh.copy_(x)
+        dh.copy_(y)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(od, op.forward(x.cuda()).cpu()) and torch.equal(om, op.transpose(y.cuda()).cpu()), k
+    op.close()
+
+
 def test_host_calls_reject_overlapping_buffers(gm):
     import torch
 
