@@ -50,6 +50,9 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--jsonl", default=None,
+                    help="also append each result line, with the run's time, arguments, GPU and host cores, "
+                         "to this JSON-lines file")
     ap.add_argument("--table1", action="store_true", help="run the Table 1 size sweep instead")
     ap.add_argument("--table1-k", default="1-12", help="sizes k of the sweep, e.g. 1-12 or 3,6,12")
     ap.add_argument("--table1-stations", type=int, default=16,
@@ -311,6 +314,26 @@ def oracle_dense_timings(names=("grav16", "mag64"), budget_s: float = 2.0):
 
 
 # ----------------------------------------------------------------------------- reference arm
+def gpu_name():
+    try:
+        import torch
+
+        return torch.cuda.get_device_name(0) if torch.cuda.is_available() else None
+    except Exception:  # the record is informational
+        return None
+
+
+def emit(line, args):
+    """Prints one result line; with --jsonl also appends it, with a record of the run, to that file."""
+    print(json.dumps(line), flush=True)
+    if getattr(args, "jsonl", None):
+        rec = dict(line)
+        rec["record"] = {"time_utc": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()), "argv": sys.argv[1:],
+                         "gpu": gpu_name(), "host_cores": os.cpu_count()}
+        with open(args.jsonl, "a") as f:
+            f.write(json.dumps(rec) + "\n")
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -336,7 +359,7 @@ def run_reference(args):
                                        f"({per_thread} per thread, binary128), scaled to the m*n entries of one "
                                        f"product"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+    emit(line, args)
     return 0
 
 
@@ -670,8 +693,8 @@ def run_ours(args):
                 "config": {**workload_config(w, inf), "parallelism": f"replicas{world}" if world > 1 else "1 GPU",
                            "timing": timing_mode},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-                "clocks": clk, **extra}
-        print(json.dumps(line))
+                "clocks": clk, "gpu": gpu_name(), **extra}
+        emit(line, args)
     op.close()
     if world > 1:
         dist.destroy_process_group()
@@ -799,7 +822,7 @@ def run_table1(args):
             t_or += time.perf_counter() - t0
             cells += len(idx)
         row["oracle_dense"] = {"applies_per_s": 1.0 / (t_or / (cells * w.m) * w.m * w.n), "cores": O.threads()}
-        print(json.dumps(row), flush=True)
+        emit(row, args)
     return 0
 
 

@@ -45,19 +45,23 @@ cudaError_t forward_fast_t(gm_plan *p, const io_t<R> *m, io_t<R> *d, cudaStream_
     C *B = static_cast<C *>(p->work_small);
     C *part = static_cast<C *>(p->work_part);
     const C *S = static_cast<const C *>(p->spec);
-    int t = timing_begin(p, s, K_FWD_ROWS);
     const XOps<R> *xo = x_ops<R>(g.NPx);
     const YOps<R> *yo = y_ops<R>(g.NPy);
     if (!xo || !yo) return cudaErrorNotSupported;
-    CK(xo->r2c(m, g.ny, g.nx, g.nz, A, g.nyp, p->tw_x, s));
+    // (each launch is bracketed by timing_begin / timing_end, also when it fails)
+    int t = timing_begin(p, s, K_FWD_ROWS);
+    cudaError_t e = xo->r2c(m, g.ny, g.nx, g.nz, A, g.nyp, p->tw_x, s);
     timing_end(p, s, t);
+    CK(e);
     t = timing_begin(p, s, K_FWD_COLS);
-    CK(yo->fwd_mac(p, A, S, part, B, s));
+    e = yo->fwd_mac(p, A, S, part, B, s);
     timing_end(p, s, t);
+    CK(e);
     t = timing_begin(p, s, K_FWD_C2R);
     // B is [kx][j]: element (k, row j) at k*sy + j
-    CK(xo->c2r(B, g.sy, 0, 1, g.sy, 1, d, g.sx, 1.0 / ((double)g.NPx * g.NPy), p->tw_x, false, s));
+    e = xo->c2r(B, g.sy, 0, 1, g.sy, 1, d, g.sx, 1.0 / ((double)g.NPx * g.NPy), p->tw_x, false, s);
     timing_end(p, s, t);
+    CK(e);
     *nl = 3;
     return cudaSuccess;
 }
@@ -69,21 +73,24 @@ cudaError_t transpose_fast_t(gm_plan *p, const io_t<R> *d, io_t<R> *m, cudaStrea
     C *D1 = static_cast<C *>(p->work_small_tr);
     C *A2 = static_cast<C *>(p->work_big_tr);
     const C *S = static_cast<const C *>(p->spec);
-    int t = timing_begin(p, s, K_TR_ROWS);
     const XOps<R> *xo = x_ops<R>(g.NPx);
     const YOps<R> *yo = y_ops<R>(g.NPy);
     if (!xo || !yo) return cudaErrorNotSupported;
-    CK(xo->r2c(d, g.sy, g.sx, 1, D1, g.sy, p->tw_x, s));
+    int t = timing_begin(p, s, K_TR_ROWS);
+    cudaError_t e = xo->r2c(d, g.sy, g.sx, 1, D1, g.sy, p->tw_x, s);
     timing_end(p, s, t);
+    CK(e);
     t = timing_begin(p, s, K_TR_COLS);
-    CK(yo->tr(p, D1, S, A2, s));
+    e = yo->tr(p, D1, S, A2, s);
     timing_end(p, s, t);
+    CK(e);
     t = timing_begin(p, s, K_TR_C2R);
     // A2 is [kx][r][q] with column pitch nyp: element (k, layer r, row q) at (k*nz + r)*nyp + q
     // A2 is dead once read: its lines are dropped from L2 instead of being written back
-    CK(xo->c2r(A2, (long long)g.nz * g.nyp, g.nyp, 1, g.ny, g.nz, m, g.nx, 1.0 / ((double)g.NPx * g.NPy), p->tw_x,
-               true, s));
+    e = xo->c2r(A2, (long long)g.nz * g.nyp, g.nyp, 1, g.ny, g.nz, m, g.nx, 1.0 / ((double)g.NPx * g.NPy), p->tw_x,
+                true, s);
     timing_end(p, s, t);
+    CK(e);
     *nl = 3;
     return cudaSuccess;
 }

@@ -221,7 +221,16 @@ gm_status gm_validate_params(const gm_params *p) {
 
 void gm_set_memory_limit(size_t bytes) { g_mem_limit = bytes; }
 
+// NVTX range around one C-ABI call (the kernels it launches carry ranges of their own).
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
+
 gm_handle grav_mag_setup_ex(const gm_params *prm) {
+    NvtxScope nv("grav_mag_setup_ex");
     if (gm_validate_params(prm) != GM_OK) return nullptr;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
@@ -407,6 +416,7 @@ static gm_status check_apply(gm_handle h, const void *in, size_t nin, const void
 }
 
 gm_status apply_forward(gm_handle h, const void *m_dev, void *d_dev, void *stream) {
+    NvtxScope nv("apply_forward");
     if (!h) return fail(GM_EINVAL, "handle is NULL");
     const size_t n = (size_t)h->geo.nx * h->geo.ny * h->geo.nz, m = (size_t)h->geo.sx * h->geo.sy;
     gm_status st = check_apply(h, m_dev, n, d_dev, m);
@@ -421,6 +431,7 @@ gm_status apply_forward(gm_handle h, const void *m_dev, void *d_dev, void *strea
 }
 
 gm_status apply_transpose(gm_handle h, const void *d_dev, void *m_dev, void *stream) {
+    NvtxScope nv("apply_transpose");
     if (!h) return fail(GM_EINVAL, "handle is NULL");
     const size_t n = (size_t)h->geo.nx * h->geo.ny * h->geo.nz, m = (size_t)h->geo.sx * h->geo.sy;
     gm_status st = check_apply(h, d_dev, m, m_dev, n);
@@ -455,6 +466,8 @@ static void *device_view_of_pinned(const void *p) {
 // direction came on the same stream with nothing of this direction in between (it already made
 // `stream` wait for it, and the kernel stream keeps the calls in order).
 static gm_status host_apply(gm_handle h, const void *in_host, void *out_host, void *stream, bool fwd, bool sync) {
+    NvtxScope nv(fwd ? (sync ? "apply_forward_host" : "apply_forward_host_async")
+                     : (sync ? "apply_transpose_host" : "apply_transpose_host_async"));
     if (!h) return fail(GM_EINVAL, "handle is NULL");
     if (!in_host || !out_host) return fail(GM_EINVAL, "NULL buffer");
     const size_t rel = h->precision == GM_F32 ? sizeof(float) : sizeof(double);
@@ -621,6 +634,7 @@ gm_status gm_copy_spectrum(gm_handle h, void *host_out, size_t bytes) {
 
 gm_status gm_cgls(gm_handle h, const void *d_dev, const void *x0_dev, void *x_dev, double alpha, int iters,
                   double *resid_host, void *stream) {
+    NvtxScope nv("gm_cgls");
     if (!h) return fail(GM_EINVAL, "handle is NULL");
     if (!d_dev || !x_dev) return fail(GM_EINVAL, "NULL buffer");
     if (iters < 0 || !(alpha >= 0) || !std::isfinite(alpha)) return fail(GM_EINVAL, "iters >= 0 and alpha >= 0 required");
@@ -640,6 +654,7 @@ gm_status gm_cgls(gm_handle h, const void *d_dev, const void *x0_dev, void *x_de
 
 gm_status gm_cgls_noalloc(gm_handle h, const void *d_dev, const void *x0_dev, void *x_dev, double alpha,
                           int iters, double *resid_host, void *stream) {
+    NvtxScope nv("gm_cgls_noalloc");
     if (!h) return fail(GM_EINVAL, "handle is NULL");
     if (!d_dev || !x_dev) return fail(GM_EINVAL, "NULL buffer");
     if (iters < 0 || !(alpha >= 0) || !std::isfinite(alpha)) return fail(GM_EINVAL, "iters >= 0 and alpha >= 0 required");

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 #include <atomic>
@@ -94,8 +95,11 @@ inline void timing_record(cudaEvent_t e, cudaStream_t s) {
         cudaEventRecord(e, s);
 }
 
-// Records the "before" event of a timed launch; returns the slot or -1.
+// Opens the NVTX range of one kernel launch (named for the kernel) and, when per-kernel timing is
+// enabled, records the "before" event on s; returns the timing slot or -1.  Every call is paired
+// with timing_end.
 inline int timing_begin(gm_plan *p, cudaStream_t s, int kid) {
+    nvtxRangePushA(kKernelNames[kid]);
     if (p->tused >= (int)p->tkid.size()) return -1;
     int slot = p->tused++;
     p->tkid[slot] = kid;
@@ -104,6 +108,7 @@ inline int timing_begin(gm_plan *p, cudaStream_t s, int kid) {
 }
 inline void timing_end(gm_plan *p, cudaStream_t s, int slot) {
     if (slot >= 0) timing_record(p->tev[2 * slot + 1], s);
+    nvtxRangePop();
 }
 }  // namespace gm
 

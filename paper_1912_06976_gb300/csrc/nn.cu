@@ -19,6 +19,7 @@
 // The element-wise steps (scaling, up-sampling, ReLU masks, loss, Adam) are plain CUDA-core kernels.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdint>
@@ -916,9 +917,18 @@ bool dev_alloc(float **p, size_t elems, size_t *total) {
 
 }  // namespace
 
+// NVTX range around one C-ABI call.
+struct NetNvtx {
+    explicit NetNvtx(const char *name) { nvtxRangePushA(name); }
+    ~NetNvtx() { nvtxRangePop(); }
+    NetNvtx(const NetNvtx &) = delete;
+    NetNvtx &operator=(const NetNvtx &) = delete;
+};
+
 extern "C" {
 
 gm_net_handle gm_net_create(int grid, int depth, int max_batch, unsigned long long seed) {
+    NetNvtx nv("gm_net_create");
     if (grid < 16 || grid > 1024 || grid % 16 || depth != 16 || max_batch < 1 ||
         (long long)max_batch * 256 * grid * grid >= (1LL << 31)) {
         nn_fail(GM_EINVAL, "gm_net_create: grid must be a multiple of 16 in [16, 1024], depth 16, "
@@ -1027,6 +1037,7 @@ gm_status gm_net_set_scales(gm_net_handle net, float in_scale, float out_scale) 
 }
 
 gm_status gm_net_forward(gm_net_handle net, const float *d_dev, float *m_dev, int batch, void *stream) {
+    NetNvtx nv("gm_net_forward");
     if (!net || !d_dev || !m_dev || batch < 1 || batch > net->max_batch)
         return nn_fail(GM_EINVAL, "gm_net_forward: null pointer or batch outside [1, max_batch]");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1040,6 +1051,7 @@ gm_status gm_net_forward(gm_net_handle net, const float *d_dev, float *m_dev, in
 
 gm_status gm_net_train_step(gm_net_handle net, const float *d_dev, const float *m_dev, int count,
                             const int32_t *index_dev, int batch, float lr, float *loss_host, void *stream) {
+    NetNvtx nv("gm_net_train_step");
     if (!net || !d_dev || !m_dev || batch < 1 || batch > net->max_batch || !(lr >= 0.f) || !std::isfinite(lr) ||
         count < 1 || (!index_dev && batch > count))
         return nn_fail(GM_EINVAL, "gm_net_train_step: null pointer, batch outside [1, max_batch], batch > count "
