@@ -455,6 +455,264 @@ __global__ void k_sum_chunks(const float *__restrict__ part, float *__restrict__
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Convolutions with one output channel (the network's last layer) on the CUDA cores.  The GEMM
+// view of such a layer has one useful column: the tensor-core kernels would pad it to 16 and
+// gather 27 x CI operand rows per position for a single product each.  Here each input value is
+// read into shared memory once per plane and reused from registers across the three x taps.
+// Stride 1, 3 x 3 in-plane taps with padding 1, KD in {1, 3} with padding KD / 2, input optionally
+// nearest up-sampled (factor 1 or 2 per axis: the stored tensor is read at coordinate >> shift).
+// Weights are the BF16 values the tensor-core kernels use; products and sums are FP32.
+struct DirectConv {
+    int N, CI, KD;
+    int OD, OH, OW;     // output = up-sampled input size
+    int LD, LH, LW;     // stored input
+    int us0, us1, us2;  // up-sampling shifts
+    int relu;
+};
+constexpr int kDirThreads = 256;
+constexpr int kDirXS = 16;  // consecutive x positions per work item
+
+// Shared memory of the three kernels (floats): WGRAD g plane + KD stored x planes; FWD weights +
+// KD stored x planes of one channel; DGRAD weights + KD g planes.
+__host__ __device__ inline size_t direct_smem_floats(int mode, const DirectConv &c) {
+    const size_t plane = (size_t)c.OH * c.OW, lplane = (size_t)c.LH * c.LW;
+    if (mode == WGRAD) return plane + (size_t)c.KD * lplane;
+    if (mode == FWD) return (size_t)c.CI * 27 + (size_t)c.KD * lplane;
+    return (size_t)c.CI * 27 + (size_t)c.KD * plane;
+}
+
+// Sum over the block (warp shuffles, then the warps in order: a fixed order); the result is valid
+// in thread 0.  red: kDirThreads / 32 floats of shared memory.
+__device__ __forceinline__ float dir_block_sum(float v, float *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float s = 0.f;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kDirThreads / 32; ++k) s += red[k];
+    __syncthreads();
+    return s;
+}
+
+// Weight gradient, block (chunk = n * OD + oz, ci):
+//   part[chunk][ci][tap] = SUM over the (oy, ox) plane of g(n, oz, oy, ox) x(n, ci, oz + kz - PD, oy + ky - 1,
+//   ox + kx - 1) (zero outside), tap = kz * 9 + ky * 3 + kx;  with ci = 0 also bpart[chunk] = SUM of g.
+__global__ void __launch_bounds__(kDirThreads) k_wgrad_co1(const float *__restrict__ x, const float *__restrict__ g,
+                                                           DirectConv c, float *__restrict__ part,
+                                                           float *__restrict__ bpart) {
+    extern __shared__ float dsm[];
+    __shared__ float red[kDirThreads / 32];
+    const int chunk = blockIdx.x, ci = blockIdx.y;
+    const int n = chunk / c.OD, oz = chunk - n * c.OD;
+    const int PD = c.KD / 2, taps = c.KD * 9;
+    const int plane = c.OH * c.OW, lplane = c.LH * c.LW;
+    float *gs = dsm;          // [OH][OW]
+    float *xs = gs + plane;   // [KD][LH][LW]
+    const float *gp = g + (size_t)chunk * plane;
+    for (int i = threadIdx.x; i < plane; i += kDirThreads) gs[i] = gp[i];
+    for (int kz = 0; kz < c.KD; ++kz) {
+        const int iz = oz + kz - PD;
+        const bool in = iz >= 0 && iz < c.OD;
+        const float *xp = x + (((size_t)n * c.CI + ci) * c.LD + (in ? (iz >> c.us0) : 0)) * lplane;
+        for (int i = threadIdx.x; i < lplane; i += kDirThreads) xs[kz * lplane + i] = in ? xp[i] : 0.f;
+    }
+    __syncthreads();
+    float acc[27];
+#pragma unroll
+    for (int t = 0; t < 27; ++t) acc[t] = 0.f;
+    float gsum = 0.f;
+    const int segs = (c.OW + kDirXS - 1) / kDirXS;
+    for (int it = threadIdx.x; it < c.OH * segs; it += kDirThreads) {
+        const int oy = it / segs, x0 = (it - oy * segs) * kDirXS;
+        float gr[kDirXS];
+#pragma unroll
+        for (int j = 0; j < kDirXS; ++j) {
+            gr[j] = x0 + j < c.OW ? gs[oy * c.OW + x0 + j] : 0.f;
+            gsum += gr[j];
+        }
+#pragma unroll
+        for (int kz = 0; kz < 3; ++kz) {
+            if (kz < c.KD) {
+#pragma unroll
+                for (int ky = 0; ky < 3; ++ky) {
+                    const int iy = oy + ky - 1;
+                    if (iy >= 0 && iy < c.OH) {
+                        const float *row = xs + kz * lplane + (iy >> c.us1) * c.LW;
+                        float r[kDirXS + 2];
+#pragma unroll
+                        for (int j = 0; j < kDirXS + 2; ++j) {
+                            const int ix = x0 - 1 + j;
+                            r[j] = (ix >= 0 && ix < c.OW) ? row[ix >> c.us2] : 0.f;
+                        }
+#pragma unroll
+                        for (int kx = 0; kx < 3; ++kx) {
+                            float sum = 0.f;
+#pragma unroll
+                            for (int j = 0; j < kDirXS; ++j) sum = fmaf(gr[j], r[j + kx], sum);
+                            acc[kz * 9 + ky * 3 + kx] += sum;
+                        }
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+        if (t < taps) {  // the same in every thread
+            const float v = dir_block_sum(acc[t], red);
+            if (threadIdx.x == 0) part[((size_t)chunk * c.CI + ci) * taps + t] = v;
+        }
+    }
+    if (ci == 0) {
+        const float v = dir_block_sum(gsum, red);
+        if (threadIdx.x == 0) bpart[chunk] = v;
+    }
+}
+
+// Forward, block chunk = n * OD + oz:  out(n, oz, oy, ox) = b + SUM_{ci, tap} w[ci][tap]
+// x(n, ci, oz + kz - PD, oy + ky - 1, ox + kx - 1), ReLU optional.  wf: the packed FWD weights of
+// the layer's one output row, element (tap, ci) at tap * CI + ci.
+__global__ void __launch_bounds__(kDirThreads) k_fwd_co1(const float *__restrict__ x, const __nv_bfloat16 *__restrict__ wf,
+                                                         const float *__restrict__ bias, DirectConv c,
+                                                         float *__restrict__ out) {
+    extern __shared__ float dsm[];
+    const int chunk = blockIdx.x;
+    const int n = chunk / c.OD, oz = chunk - n * c.OD;
+    const int PD = c.KD / 2, taps = c.KD * 9;
+    const int lplane = c.LH * c.LW;
+    float *ws = dsm;               // [CI][27]
+    float *xs = ws + c.CI * 27;    // [KD][LH][LW] of the current channel
+    for (int i = threadIdx.x; i < c.CI * taps; i += kDirThreads) {
+        const int ci = i / taps, tap = i - ci * taps;
+        ws[ci * 27 + tap] = bf(wf[(size_t)tap * c.CI + ci]);
+    }
+    const int segs = (c.OW + kDirXS - 1) / kDirXS;
+    const int items = c.OH * segs;
+    const float b0 = bias[0];
+    // every thread keeps the sums of its work items; at most two per thread for planes of up to
+    // 2 * kDirThreads * kDirXS positions (the host checks this)
+    float acc[2][kDirXS];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int j = 0; j < kDirXS; ++j) acc[q][j] = b0;
+    for (int ci = 0; ci < c.CI; ++ci) {
+        __syncthreads();  // the previous channel's planes are no longer read
+        for (int kz = 0; kz < c.KD; ++kz) {
+            const int iz = oz + kz - PD;
+            const bool in = iz >= 0 && iz < c.OD;
+            const float *xp = x + (((size_t)n * c.CI + ci) * c.LD + (in ? (iz >> c.us0) : 0)) * lplane;
+            for (int i = threadIdx.x; i < lplane; i += kDirThreads) xs[kz * lplane + i] = in ? xp[i] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int it = threadIdx.x + q * kDirThreads;
+            if (it < items) {
+                const int oy = it / segs, x0 = (it - oy * segs) * kDirXS;
+#pragma unroll
+                for (int kz = 0; kz < 3; ++kz) {
+                    if (kz < c.KD) {
+#pragma unroll
+                        for (int ky = 0; ky < 3; ++ky) {
+                            const int iy = oy + ky - 1;
+                            if (iy >= 0 && iy < c.OH) {
+                                const float *row = xs + kz * lplane + (iy >> c.us1) * c.LW;
+                                const float *wr = ws + ci * 27 + kz * 9 + ky * 3;
+                                const float w0 = wr[0], w1 = wr[1], w2 = wr[2];
+                                float r[kDirXS + 2];
+#pragma unroll
+                                for (int j = 0; j < kDirXS + 2; ++j) {
+                                    const int ix = x0 - 1 + j;
+                                    r[j] = (ix >= 0 && ix < c.OW) ? row[ix >> c.us2] : 0.f;
+                                }
+#pragma unroll
+                                for (int j = 0; j < kDirXS; ++j)
+                                    acc[q][j] = fmaf(w2, r[j + 2], fmaf(w1, r[j + 1], fmaf(w0, r[j], acc[q][j])));
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    const size_t plane = (size_t)c.OH * c.OW;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int it = threadIdx.x + q * kDirThreads;
+        if (it < items) {
+            const int oy = it / segs, x0 = (it - oy * segs) * kDirXS;
+            float *o = out + (size_t)chunk * plane + (size_t)oy * c.OW;
+#pragma unroll
+            for (int j = 0; j < kDirXS; ++j)
+                if (x0 + j < c.OW) o[x0 + j] = c.relu ? fmaxf(acc[q][j], 0.f) : acc[q][j];
+        }
+    }
+}
+
+// Data gradient at the up-sampled input, block chunk = n * OD + iz:
+//   gin(n, ci, iz, iy, ix) = SUM_tap w[ci][tap] g(n, iz + PD - kz, iy + 1 - ky, ix + 1 - kx) (zero outside).
+// wd: the packed DGRAD weights, element (ci, tap) at ci * kd + tap (one output channel).
+__global__ void __launch_bounds__(kDirThreads) k_dgrad_co1(const float *__restrict__ g, const __nv_bfloat16 *__restrict__ wd,
+                                                           int kd, DirectConv c, float *__restrict__ gin) {
+    extern __shared__ float dsm[];
+    const int chunk = blockIdx.x;
+    const int n = chunk / c.OD, iz = chunk - n * c.OD;
+    const int PD = c.KD / 2, taps = c.KD * 9;
+    const int plane = c.OH * c.OW;
+    float *ws = dsm;               // [CI][27]
+    float *gs = ws + c.CI * 27;    // [KD][OH][OW]: the g planes oz = iz + PD - kz
+    for (int i = threadIdx.x; i < c.CI * taps; i += kDirThreads) {
+        const int ci = i / taps, tap = i - ci * taps;
+        ws[ci * 27 + tap] = bf(wd[(size_t)ci * kd + tap]);
+    }
+    for (int kz = 0; kz < c.KD; ++kz) {
+        const int oz = iz + PD - kz;
+        const bool in = oz >= 0 && oz < c.OD;
+        const float *gp = g + ((size_t)n * c.OD + (in ? oz : 0)) * plane;
+        for (int i = threadIdx.x; i < plane; i += kDirThreads) gs[kz * plane + i] = in ? gp[i] : 0.f;
+    }
+    __syncthreads();
+    const int segs = (c.OW + kDirXS - 1) / kDirXS;
+    for (int it = threadIdx.x; it < c.OH * segs; it += kDirThreads) {
+        const int iy = it / segs, x0 = (it - iy * segs) * kDirXS;
+        for (int ci = 0; ci < c.CI; ++ci) {
+            float acc[kDirXS];
+#pragma unroll
+            for (int j = 0; j < kDirXS; ++j) acc[j] = 0.f;
+#pragma unroll
+            for (int kz = 0; kz < 3; ++kz) {
+                if (kz < c.KD) {
+#pragma unroll
+                    for (int ky = 0; ky < 3; ++ky) {
+                        const int oy = iy + 1 - ky;
+                        if (oy >= 0 && oy < c.OH) {
+                            const float *row = gs + kz * plane + oy * c.OW;
+                            const float *wr = ws + ci * 27 + kz * 9 + ky * 3;
+                            const float w0 = wr[0], w1 = wr[1], w2 = wr[2];
+                            // r[m] = g at ox = x0 - 1 + m; ix = x0 + j takes ox = ix + 1 - kx = x0 + j + 1 - kx
+                            float r[kDirXS + 2];
+#pragma unroll
+                            for (int m = 0; m < kDirXS + 2; ++m) {
+                                const int ox = x0 - 1 + m;
+                                r[m] = (ox >= 0 && ox < c.OW) ? row[ox] : 0.f;
+                            }
+#pragma unroll
+                            for (int j = 0; j < kDirXS; ++j)
+                                acc[j] = fmaf(w2, r[j], fmaf(w1, r[j + 1], fmaf(w0, r[j + 2], acc[j])));
+                        }
+                    }
+                }
+            }
+            float *o = gin + (((size_t)n * c.CI + ci) * c.OD + iz) * plane + (size_t)iy * c.OW;
+#pragma unroll
+            for (int j = 0; j < kDirXS; ++j)
+                if (x0 + j < c.OW) o[x0 + j] = acc[j];
+        }
+    }
+}
+
 // adjoint of nearest up-sampling: gin[c][z][y][x] = SUM of gout over its (fz, fy, fx) block
 // (sizes below 2^31, which gm_net_create guarantees)
 __global__ void k_upsample_bwd(const float *__restrict__ gout, float *__restrict__ gin, int NC, int D, int H, int W,
@@ -724,6 +982,41 @@ int log2_exact(int v) {
     return l;
 }
 
+// The one-output-channel layers that the CUDA-core kernels take (see k_wgrad_co1): stride 1,
+// "same" padding, 3 x 3 in-plane taps, at most two work items of kDirXS positions per thread in
+// the forward kernel, shared memory within the opt-in limit.
+constexpr size_t kDirSmemMax = 200 * 1024;
+
+gm::nn::DirectConv direct_view(const Layer &l, int N) {
+    gm::nn::DirectConv c{};
+    c.N = N;
+    c.CI = l.d.CI;
+    c.KD = l.d.KD;
+    c.OD = l.d.OD;
+    c.OH = l.d.OH;
+    c.OW = l.d.OW;
+    c.LD = l.in_d;
+    c.LH = l.in_h;
+    c.LW = l.in_w;
+    c.us0 = l.up[0] == 2 ? 1 : 0;
+    c.us1 = l.up[1] == 2 ? 1 : 0;
+    c.us2 = l.up[2] == 2 ? 1 : 0;
+    c.relu = l.relu ? 1 : 0;
+    return c;
+}
+
+bool direct_ok(const Layer &l) {
+    const ConvDims &d = l.d;
+    if (d.CO != 1 || d.SD != 1 || d.SH != 1 || d.SW != 1 || d.KH != 3 || d.KW != 3 || d.PH != 1 || d.PW != 1)
+        return false;
+    if ((d.KD != 1 && d.KD != 3) || d.PD != d.KD / 2 || d.OD != d.ID || d.OH != d.IH || d.OW != d.IW) return false;
+    if ((long long)d.OH * ((d.OW + gm::nn::kDirXS - 1) / gm::nn::kDirXS) > 2LL * gm::nn::kDirThreads) return false;
+    const gm::nn::DirectConv c = direct_view(l, 1);
+    for (int mode = 0; mode < 3; ++mode)
+        if (sizeof(float) * gm::nn::direct_smem_floats(mode, c) > kDirSmemMax) return false;
+    return true;
+}
+
 // WGRAD split of the N * osz positions: enough chunks for about two waves of CTAs, each a
 // multiple of 64 positions between 256 and 8192
 int wgrad_chunk(const Layer &l, int N) {
@@ -824,9 +1117,30 @@ int launch_tc(const Layer &l, int N, const __nv_bfloat16 *wpk, const float *bias
     return 2;
 }
 
+// Weight-gradient partials of layer l for a batch of N: one per (n, output plane) on the CUDA-core
+// path, one per position chunk on the tensor cores.
 int wgrad_chunks(const Layer &l, int N) {
+    if (direct_ok(l)) return N * l.d.OD;
     const long long Q = (long long)N * l.d.OD * l.d.OH * l.d.OW;
     return (int)((Q + wgrad_chunk(l, N) - 1) / wgrad_chunk(l, N));
+}
+
+// One convolution of layer l in mode MODE: the CUDA-core kernels for a one-output-channel layer,
+// else the tensor-core GEMM (launch_tc, same arguments); returns the launches made.
+template <int MODE>
+int launch_conv(const Layer &l, int N, const __nv_bfloat16 *wpk, const float *bias, const float *act,
+                const float *grad, float *out, float *out2, int *err, cudaStream_t s) {
+    if (!direct_ok(l)) return launch_tc<MODE>(l, N, wpk, bias, act, grad, out, out2, err, s);
+    const gm::nn::DirectConv c = direct_view(l, N);
+    const size_t smem = sizeof(float) * gm::nn::direct_smem_floats(MODE, c);
+    const int planes = N * l.d.OD;
+    if (MODE == gm::nn::FWD)
+        gm::nn::k_fwd_co1<<<planes, gm::nn::kDirThreads, smem, s>>>(act, wpk, bias, c, out);
+    else if (MODE == gm::nn::DGRAD)
+        gm::nn::k_dgrad_co1<<<planes, gm::nn::kDirThreads, smem, s>>>(grad, wpk, l.kd, c, out);
+    else
+        gm::nn::k_wgrad_co1<<<dim3(planes, l.d.CI), gm::nn::kDirThreads, smem, s>>>(act, grad, c, out, out2);
+    return 1;
 }
 
 cudaError_t set_tc_smem_limits() {
@@ -837,6 +1151,9 @@ cudaError_t set_tc_smem_limits() {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kerns[mode], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      2 * gm::nn::conv_stage_bytes(mode, 256));
+    const void *direct[3] = {(void *)gm::nn::k_fwd_co1, (void *)gm::nn::k_dgrad_co1, (void *)gm::nn::k_wgrad_co1};
+    for (const void *k : direct)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDirSmemMax);
     return e;
 }
 
@@ -851,8 +1168,8 @@ int forward_all(gm_net *net, const float *d_dev, const int *idx, int count, int 
     for (size_t k = 0; k < L; ++k) {
         const Layer &l = net->layers[k];
         float *dst = (k + 1 < L) ? net->x[k + 1] : net->y;
-        nl += launch_tc<gm::nn::FWD>(l, N, net->wf + l.f_off, net->w + l.b_off, net->x[k], nullptr, dst, net->kpart,
-                                     net->tc_err, s);
+        nl += launch_conv<gm::nn::FWD>(l, N, net->wf + l.f_off, net->w + l.b_off, net->x[k], nullptr, dst,
+                                       net->kpart, net->tc_err, s);
     }
     return nl;
 }
@@ -873,20 +1190,20 @@ int backward_all(gm_net *net, int N, cudaStream_t s) {
         const int chunks = wgrad_chunks(l, N);
         float *dwp = net->wpart;
         float *dbp = net->wpart + (size_t)chunks * l.nw;
-        launch_tc<gm::nn::WGRAD>(l, N, nullptr, nullptr, net->x[k], g, dwp, dbp, net->tc_err, s);
+        launch_conv<gm::nn::WGRAD>(l, N, nullptr, nullptr, net->x[k], g, dwp, dbp, net->tc_err, s);
         gm::nn::k_sum_chunks<<<grid1(l.nw), 256, 0, s>>>(dwp, net->gw + l.w_off, l.nw, chunks);
         gm::nn::k_sum_chunks<<<grid1(l.d.CO), 256, 0, s>>>(dbp, net->gw + l.b_off, l.d.CO, chunks);
         nl += 3;
         if (k == 0) break;  // no gradient with respect to the data
         if (l.upsampled()) {
-            nl += launch_tc<gm::nn::DGRAD>(l, N, net->wd + l.d_off, nullptr, nullptr, g, net->gu[k], net->kpart,
-                                           net->tc_err, s);
+            nl += launch_conv<gm::nn::DGRAD>(l, N, net->wd + l.d_off, nullptr, nullptr, g, net->gu[k], net->kpart,
+                                             net->tc_err, s);
             gm::nn::k_upsample_bwd<<<grid1(l.in_low(N)), 256, 0, s>>>(net->gu[k], net->gx[k], N * l.d.CI, l.in_d,
                                                                       l.in_h, l.in_w, l.up[0], l.up[1], l.up[2]);
             ++nl;
         } else {
-            nl += launch_tc<gm::nn::DGRAD>(l, N, net->wd + l.d_off, nullptr, nullptr, g, net->gx[k], net->kpart,
-                                           net->tc_err, s);
+            nl += launch_conv<gm::nn::DGRAD>(l, N, net->wd + l.d_off, nullptr, nullptr, g, net->gx[k], net->kpart,
+                                             net->tc_err, s);
         }
         g = net->gx[k];
     }
@@ -1267,15 +1584,15 @@ gm_status gm_conv3d(int mode, int N, int CI, int CO, int ID, int IH, int IW, int
                 e = cudaMalloc(&zero, sizeof(float) * CO);
                 if (e == cudaSuccess) e = cudaMemsetAsync(zero, 0, sizeof(float) * CO, s);
             }
-            if (e == cudaSuccess) launch_tc<gm::nn::FWD>(l, N, wf, b ? b : zero, x, nullptr, out, kpart, err, s);
+            if (e == cudaSuccess) launch_conv<gm::nn::FWD>(l, N, wf, b ? b : zero, x, nullptr, out, kpart, err, s);
             if (zero) {
                 cudaStreamSynchronize(s);
                 cudaFree(zero);
             }
         } else if (mode == 1) {
-            launch_tc<gm::nn::DGRAD>(l, N, wd, nullptr, nullptr, g, out, kpart, err, s);
+            launch_conv<gm::nn::DGRAD>(l, N, wd, nullptr, nullptr, g, out, kpart, err, s);
         } else {
-            launch_tc<gm::nn::WGRAD>(l, N, nullptr, nullptr, x, g, part, part + (size_t)chunks * l.nw, err, s);
+            launch_conv<gm::nn::WGRAD>(l, N, nullptr, nullptr, x, g, part, part + (size_t)chunks * l.nw, err, s);
             gm::nn::k_sum_chunks<<<grid1(l.nw), 256, 0, s>>>(part, out, l.nw, chunks);
             if (bias_grad)
                 gm::nn::k_sum_chunks<<<grid1(CO), 256, 0, s>>>(part + (size_t)chunks * l.nw, bias_grad, CO, chunks);
