@@ -458,8 +458,10 @@ __global__ void k_sum_chunks(const float *__restrict__ part, float *__restrict__
 // ------------------------------------------------------------------------------------------
 // Convolutions with one output channel (the network's last layer) on the CUDA cores.  The GEMM
 // view of such a layer has one useful column: the tensor-core kernels would pad it to 16 and
-// gather 27 x CI operand rows per position for a single product each.  Here each input value is
-// read into shared memory once per plane and reused from registers across the three x taps.
+// gather 27 x CI operand rows per position for a single product each.  Here the planes a block
+// needs are read into shared memory once.  A warp task is 32 consecutive x positions (one per
+// lane, so shared-memory rows are read without bank conflicts) by kDirRY rows; each input row a
+// lane loads serves the up to three output rows (y taps) it touches, from registers.
 // Stride 1, 3 x 3 in-plane taps with padding 1, KD in {1, 3} with padding KD / 2, input optionally
 // nearest up-sampled (factor 1 or 2 per axis: the stored tensor is read at coordinate >> shift).
 // Weights are the BF16 values the tensor-core kernels use; products and sums are FP32.
@@ -469,9 +471,13 @@ struct DirectConv {
     int LD, LH, LW;     // stored input
     int us0, us1, us2;  // up-sampling shifts
     int relu;
+    int planes_per_block;  // weight gradient: (n, z) planes summed by one block
 };
 constexpr int kDirThreads = 256;
-constexpr int kDirXS = 16;  // consecutive x positions per work item
+constexpr int kDirWarps = kDirThreads / 32;
+constexpr int kDirRY = 8;         // rows per warp task
+constexpr int kDirTasksMax = 16;  // forward: at most two warp tasks per warp and plane
+constexpr int kDirPre = 16;       // forward: stored input values per thread prefetched for the next channel
 
 // Shared memory of the three kernels (floats): WGRAD g plane + KD stored x planes; FWD weights +
 // KD stored x planes of one channel; DGRAD weights + KD g planes.
@@ -482,123 +488,35 @@ __host__ __device__ inline size_t direct_smem_floats(int mode, const DirectConv 
     return (size_t)c.CI * 27 + (size_t)c.KD * plane;
 }
 
-// Sum over the block (warp shuffles, then the warps in order: a fixed order); the result is valid
-// in thread 0.  red: kDirThreads / 32 floats of shared memory.
-__device__ __forceinline__ float dir_block_sum(float v, float *red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float s = 0.f;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < kDirThreads / 32; ++k) s += red[k];
-    __syncthreads();
-    return s;
+__host__ __device__ inline int dir_tasks(const DirectConv &c) {
+    return ((c.OW + 31) / 32) * ((c.OH + kDirRY - 1) / kDirRY);
 }
 
-// Weight gradient, block (chunk = n * OD + oz, ci):
-//   part[chunk][ci][tap] = SUM over the (oy, ox) plane of g(n, oz, oy, ox) x(n, ci, oz + kz - PD, oy + ky - 1,
+// Weight gradient, block (chunk, ci), chunk covering the (n, oz) planes [chunk * P, chunk * P + P):
+//   part[chunk][ci][tap] = SUM over those planes of g(n, oz, oy, ox) x(n, ci, oz + kz - PD, oy + ky - 1,
 //   ox + kx - 1) (zero outside), tap = kz * 9 + ky * 3 + kx;  with ci = 0 also bpart[chunk] = SUM of g.
 __global__ void __launch_bounds__(kDirThreads) k_wgrad_co1(const float *__restrict__ x, const float *__restrict__ g,
                                                            DirectConv c, float *__restrict__ part,
                                                            float *__restrict__ bpart) {
     extern __shared__ float dsm[];
-    __shared__ float red[kDirThreads / 32];
+    __shared__ float red[kDirWarps][28];
     const int chunk = blockIdx.x, ci = blockIdx.y;
-    const int n = chunk / c.OD, oz = chunk - n * c.OD;
     const int PD = c.KD / 2, taps = c.KD * 9;
     const int plane = c.OH * c.OW, lplane = c.LH * c.LW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int XB = (c.OW + 31) / 32, tasks = dir_tasks(c);
     float *gs = dsm;          // [OH][OW]
     float *xs = gs + plane;   // [KD][LH][LW]
-    const float *gp = g + (size_t)chunk * plane;
-    for (int i = threadIdx.x; i < plane; i += kDirThreads) gs[i] = gp[i];
-    for (int kz = 0; kz < c.KD; ++kz) {
-        const int iz = oz + kz - PD;
-        const bool in = iz >= 0 && iz < c.OD;
-        const float *xp = x + (((size_t)n * c.CI + ci) * c.LD + (in ? (iz >> c.us0) : 0)) * lplane;
-        for (int i = threadIdx.x; i < lplane; i += kDirThreads) xs[kz * lplane + i] = in ? xp[i] : 0.f;
-    }
-    __syncthreads();
     float acc[27];
 #pragma unroll
     for (int t = 0; t < 27; ++t) acc[t] = 0.f;
     float gsum = 0.f;
-    const int segs = (c.OW + kDirXS - 1) / kDirXS;
-    for (int it = threadIdx.x; it < c.OH * segs; it += kDirThreads) {
-        const int oy = it / segs, x0 = (it - oy * segs) * kDirXS;
-        float gr[kDirXS];
-#pragma unroll
-        for (int j = 0; j < kDirXS; ++j) {
-            gr[j] = x0 + j < c.OW ? gs[oy * c.OW + x0 + j] : 0.f;
-            gsum += gr[j];
-        }
-#pragma unroll
-        for (int kz = 0; kz < 3; ++kz) {
-            if (kz < c.KD) {
-#pragma unroll
-                for (int ky = 0; ky < 3; ++ky) {
-                    const int iy = oy + ky - 1;
-                    if (iy >= 0 && iy < c.OH) {
-                        const float *row = xs + kz * lplane + (iy >> c.us1) * c.LW;
-                        float r[kDirXS + 2];
-#pragma unroll
-                        for (int j = 0; j < kDirXS + 2; ++j) {
-                            const int ix = x0 - 1 + j;
-                            r[j] = (ix >= 0 && ix < c.OW) ? row[ix >> c.us2] : 0.f;
-                        }
-#pragma unroll
-                        for (int kx = 0; kx < 3; ++kx) {
-                            float sum = 0.f;
-#pragma unroll
-                            for (int j = 0; j < kDirXS; ++j) sum = fmaf(gr[j], r[j + kx], sum);
-                            acc[kz * 9 + ky * 3 + kx] += sum;
-                        }
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < 27; ++t) {
-        if (t < taps) {  // the same in every thread
-            const float v = dir_block_sum(acc[t], red);
-            if (threadIdx.x == 0) part[((size_t)chunk * c.CI + ci) * taps + t] = v;
-        }
-    }
-    if (ci == 0) {
-        const float v = dir_block_sum(gsum, red);
-        if (threadIdx.x == 0) bpart[chunk] = v;
-    }
-}
-
-// Forward, block chunk = n * OD + oz:  out(n, oz, oy, ox) = b + SUM_{ci, tap} w[ci][tap]
-// x(n, ci, oz + kz - PD, oy + ky - 1, ox + kx - 1), ReLU optional.  wf: the packed FWD weights of
-// the layer's one output row, element (tap, ci) at tap * CI + ci.
-__global__ void __launch_bounds__(kDirThreads) k_fwd_co1(const float *__restrict__ x, const __nv_bfloat16 *__restrict__ wf,
-                                                         const float *__restrict__ bias, DirectConv c,
-                                                         float *__restrict__ out) {
-    extern __shared__ float dsm[];
-    const int chunk = blockIdx.x;
-    const int n = chunk / c.OD, oz = chunk - n * c.OD;
-    const int PD = c.KD / 2, taps = c.KD * 9;
-    const int lplane = c.LH * c.LW;
-    float *ws = dsm;               // [CI][27]
-    float *xs = ws + c.CI * 27;    // [KD][LH][LW] of the current channel
-    for (int i = threadIdx.x; i < c.CI * taps; i += kDirThreads) {
-        const int ci = i / taps, tap = i - ci * taps;
-        ws[ci * 27 + tap] = bf(wf[(size_t)tap * c.CI + ci]);
-    }
-    const int segs = (c.OW + kDirXS - 1) / kDirXS;
-    const int items = c.OH * segs;
-    const float b0 = bias[0];
-    // every thread keeps the sums of its work items; at most two per thread for planes of up to
-    // 2 * kDirThreads * kDirXS positions (the host checks this)
-    float acc[2][kDirXS];
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int j = 0; j < kDirXS; ++j) acc[q][j] = b0;
-    for (int ci = 0; ci < c.CI; ++ci) {
-        __syncthreads();  // the previous channel's planes are no longer read
+    const int p_end = min(c.N * c.OD, (chunk + 1) * c.planes_per_block);
+    for (int pl = chunk * c.planes_per_block; pl < p_end; ++pl) {
+        const int n = pl / c.OD, oz = pl - n * c.OD;
+        __syncthreads();  // the previous plane is no longer read
+        const float *gp = g + (size_t)pl * plane;
+        for (int i = threadIdx.x; i < plane; i += kDirThreads) gs[i] = gp[i];
         for (int kz = 0; kz < c.KD; ++kz) {
             const int iz = oz + kz - PD;
             const bool in = iz >= 0 && iz < c.OD;
@@ -606,30 +524,148 @@ __global__ void __launch_bounds__(kDirThreads) k_fwd_co1(const float *__restrict
             for (int i = threadIdx.x; i < lplane; i += kDirThreads) xs[kz * lplane + i] = in ? xp[i] : 0.f;
         }
         __syncthreads();
+        for (int task = warp; task < tasks; task += kDirWarps) {
+            const int xb = task % XB, y0 = (task / XB) * kDirRY;
+            const int px = xb * 32 + lane;
+            float gr[kDirRY];
+#pragma unroll
+            for (int r = 0; r < kDirRY; ++r) {
+                gr[r] = (px < c.OW && y0 + r < c.OH) ? gs[(y0 + r) * c.OW + px] : 0.f;
+                gsum += gr[r];
+            }
+#pragma unroll
+            for (int kz = 0; kz < 3; ++kz) {
+                if (kz < c.KD) {
+                    const float *xpl = xs + kz * lplane;
+#pragma unroll
+                    for (int ry = 0; ry < kDirRY + 2; ++ry) {
+                        const int iy = y0 + ry - 1;  // input row; output row y0 + r takes it with ky = ry - r
+                        if (iy >= 0 && iy < c.OH) {
+                            const float *row = xpl + (iy >> c.us1) * c.LW;
+                            float v[3];
+#pragma unroll
+                            for (int kx = 0; kx < 3; ++kx) {
+                                const int ix = px + kx - 1;
+                                v[kx] = (ix >= 0 && ix < c.OW) ? row[ix >> c.us2] : 0.f;
+                            }
+#pragma unroll
+                            for (int ky = 0; ky < 3; ++ky) {
+                                const int r = ry - ky;
+                                if (r >= 0 && r < kDirRY) {
+#pragma unroll
+                                    for (int kx = 0; kx < 3; ++kx)
+                                        acc[kz * 9 + ky * 3 + kx] = fmaf(gr[r], v[kx], acc[kz * 9 + ky * 3 + kx]);
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    // block sums in a fixed order: warp shuffles, then the warps in order
+#pragma unroll
+    for (int t = 0; t < 28; ++t) {
+        float v = t < 27 ? acc[t] : gsum;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][t] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < taps || (ci == 0 && threadIdx.x == 27)) {
+        float sum = 0.f;
+        for (int w = 0; w < kDirWarps; ++w) sum += red[w][threadIdx.x];
+        if (threadIdx.x < taps)
+            part[((size_t)chunk * c.CI + ci) * taps + threadIdx.x] = sum;
+        else
+            bpart[chunk] = sum;
+    }
+}
+
+// Forward, block = plane (n, oz):  out(n, oz, oy, ox) = b + SUM_{ci, tap} w[ci][tap]
+// x(n, ci, oz + kz - PD, oy + ky - 1, ox + kx - 1), ReLU optional.  wf: the packed FWD weights of
+// the layer's one output row, element (tap, ci) at tap * CI + ci.  The next channel's stored planes
+// are loaded into registers while the current one is used.
+__global__ void __launch_bounds__(kDirThreads) k_fwd_co1(const float *__restrict__ x, const __nv_bfloat16 *__restrict__ wf,
+                                                         const float *__restrict__ bias, DirectConv c,
+                                                         float *__restrict__ out) {
+    extern __shared__ float dsm[];
+    const int pl = blockIdx.x;
+    const int n = pl / c.OD, oz = pl - n * c.OD;
+    const int PD = c.KD / 2, taps = c.KD * 9;
+    const int lplane = c.LH * c.LW, nload = c.KD * lplane;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int XB = (c.OW + 31) / 32, tasks = dir_tasks(c);
+    float *ws = dsm;               // [CI][27]
+    float *xs = ws + c.CI * 27;    // [KD][LH][LW] of the current channel
+    for (int i = threadIdx.x; i < c.CI * taps; i += kDirThreads) {
+        const int ci = i / taps, tap = i - ci * taps;
+        ws[ci * 27 + tap] = bf(wf[(size_t)tap * c.CI + ci]);
+    }
+    // element i = threadIdx.x + k * kDirThreads of a channel's KD stored planes comes from offset
+    // off[k] of that channel's stored volume (-1: outside the volume or past the planes: zero)
+    int off[kDirPre];
+#pragma unroll
+    for (int k = 0; k < kDirPre; ++k) {
+        const int i = threadIdx.x + k * kDirThreads;
+        const int kz = i / lplane, e = i - kz * lplane, iz = oz + kz - PD;
+        off[k] = (i < nload && iz >= 0 && iz < c.OD) ? (iz >> c.us0) * lplane + e : -1;
+    }
+    const size_t cstride = (size_t)c.LD * lplane;
+    const float *xn = x + (size_t)n * c.CI * cstride;
+    float pre[kDirPre];
+#pragma unroll
+    for (int k = 0; k < kDirPre; ++k) pre[k] = off[k] >= 0 ? xn[off[k]] : 0.f;
+    const float b0 = bias[0];
+    float acc[2][kDirRY];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int r = 0; r < kDirRY; ++r) acc[q][r] = b0;
+    for (int ci = 0; ci < c.CI; ++ci) {
+        __syncthreads();  // the previous channel's planes are no longer read
+#pragma unroll
+        for (int k = 0; k < kDirPre; ++k) {
+            const int i = threadIdx.x + k * kDirThreads;
+            if (i < nload) xs[i] = pre[k];
+        }
+        __syncthreads();
+        if (ci + 1 < c.CI) {
+            const float *xc = xn + (size_t)(ci + 1) * cstride;
+#pragma unroll
+            for (int k = 0; k < kDirPre; ++k) pre[k] = off[k] >= 0 ? xc[off[k]] : 0.f;
+        }
+        float w[27];
+#pragma unroll
+        for (int t = 0; t < 27; ++t) w[t] = ws[ci * 27 + t];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const int it = threadIdx.x + q * kDirThreads;
-            if (it < items) {
-                const int oy = it / segs, x0 = (it - oy * segs) * kDirXS;
+            const int task = warp + q * kDirWarps;
+            if (task < tasks) {
+                const int xb = task % XB, y0 = (task / XB) * kDirRY;
+                const int px = xb * 32 + lane;
 #pragma unroll
                 for (int kz = 0; kz < 3; ++kz) {
                     if (kz < c.KD) {
+                        const float *xpl = xs + kz * lplane;
 #pragma unroll
-                        for (int ky = 0; ky < 3; ++ky) {
-                            const int iy = oy + ky - 1;
+                        for (int ry = 0; ry < kDirRY + 2; ++ry) {
+                            const int iy = y0 + ry - 1;
                             if (iy >= 0 && iy < c.OH) {
-                                const float *row = xs + kz * lplane + (iy >> c.us1) * c.LW;
-                                const float *wr = ws + ci * 27 + kz * 9 + ky * 3;
-                                const float w0 = wr[0], w1 = wr[1], w2 = wr[2];
-                                float r[kDirXS + 2];
+                                const float *row = xpl + (iy >> c.us1) * c.LW;
+                                float v[3];
 #pragma unroll
-                                for (int j = 0; j < kDirXS + 2; ++j) {
-                                    const int ix = x0 - 1 + j;
-                                    r[j] = (ix >= 0 && ix < c.OW) ? row[ix >> c.us2] : 0.f;
+                                for (int kx = 0; kx < 3; ++kx) {
+                                    const int ix = px + kx - 1;
+                                    v[kx] = (ix >= 0 && ix < c.OW) ? row[ix >> c.us2] : 0.f;
                                 }
 #pragma unroll
-                                for (int j = 0; j < kDirXS; ++j)
-                                    acc[q][j] = fmaf(w2, r[j + 2], fmaf(w1, r[j + 1], fmaf(w0, r[j], acc[q][j])));
+                                for (int ky = 0; ky < 3; ++ky) {
+                                    const int r = ry - ky;
+                                    if (r >= 0 && r < kDirRY) {
+                                        const float *wk = w + kz * 9 + ky * 3;
+                                        acc[q][r] = fmaf(wk[2], v[2], fmaf(wk[1], v[1], fmaf(wk[0], v[0], acc[q][r])));
+                                    }
+                                }
                             }
                         }
                     }
@@ -640,27 +676,34 @@ __global__ void __launch_bounds__(kDirThreads) k_fwd_co1(const float *__restrict
     const size_t plane = (size_t)c.OH * c.OW;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-        const int it = threadIdx.x + q * kDirThreads;
-        if (it < items) {
-            const int oy = it / segs, x0 = (it - oy * segs) * kDirXS;
-            float *o = out + (size_t)chunk * plane + (size_t)oy * c.OW;
+        const int task = warp + q * kDirWarps;
+        if (task < tasks) {
+            const int xb = task % XB, y0 = (task / XB) * kDirRY;
+            const int px = xb * 32 + lane;
+            if (px < c.OW) {
 #pragma unroll
-            for (int j = 0; j < kDirXS; ++j)
-                if (x0 + j < c.OW) o[x0 + j] = c.relu ? fmaxf(acc[q][j], 0.f) : acc[q][j];
+                for (int r = 0; r < kDirRY; ++r)
+                    if (y0 + r < c.OH) {
+                        const float v = acc[q][r];
+                        out[(size_t)pl * plane + (size_t)(y0 + r) * c.OW + px] = c.relu ? fmaxf(v, 0.f) : v;
+                    }
+            }
         }
     }
 }
 
-// Data gradient at the up-sampled input, block chunk = n * OD + iz:
+// Data gradient at the up-sampled input, block = plane (n, iz):
 //   gin(n, ci, iz, iy, ix) = SUM_tap w[ci][tap] g(n, iz + PD - kz, iy + 1 - ky, ix + 1 - kx) (zero outside).
 // wd: the packed DGRAD weights, element (ci, tap) at ci * kd + tap (one output channel).
 __global__ void __launch_bounds__(kDirThreads) k_dgrad_co1(const float *__restrict__ g, const __nv_bfloat16 *__restrict__ wd,
                                                            int kd, DirectConv c, float *__restrict__ gin) {
     extern __shared__ float dsm[];
-    const int chunk = blockIdx.x;
-    const int n = chunk / c.OD, iz = chunk - n * c.OD;
+    const int pl = blockIdx.x;
+    const int n = pl / c.OD, iz = pl - n * c.OD;
     const int PD = c.KD / 2, taps = c.KD * 9;
     const int plane = c.OH * c.OW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int XB = (c.OW + 31) / 32, tasks = dir_tasks(c);
     float *ws = dsm;               // [CI][27]
     float *gs = ws + c.CI * 27;    // [KD][OH][OW]: the g planes oz = iz + PD - kz
     for (int i = threadIdx.x; i < c.CI * taps; i += kDirThreads) {
@@ -674,41 +717,50 @@ __global__ void __launch_bounds__(kDirThreads) k_dgrad_co1(const float *__restri
         for (int i = threadIdx.x; i < plane; i += kDirThreads) gs[kz * plane + i] = in ? gp[i] : 0.f;
     }
     __syncthreads();
-    const int segs = (c.OW + kDirXS - 1) / kDirXS;
-    for (int it = threadIdx.x; it < c.OH * segs; it += kDirThreads) {
-        const int iy = it / segs, x0 = (it - iy * segs) * kDirXS;
-        for (int ci = 0; ci < c.CI; ++ci) {
-            float acc[kDirXS];
+    for (int ci = 0; ci < c.CI; ++ci) {
+        float w[27];
 #pragma unroll
-            for (int j = 0; j < kDirXS; ++j) acc[j] = 0.f;
+        for (int t = 0; t < 27; ++t) w[t] = ws[ci * 27 + t];
+        float *o = gin + (((size_t)n * c.CI + ci) * c.OD + iz) * plane;
+        for (int task = warp; task < tasks; task += kDirWarps) {
+            const int xb = task % XB, y0 = (task / XB) * kDirRY;
+            const int px = xb * 32 + lane;
+            float acc[kDirRY];
+#pragma unroll
+            for (int r = 0; r < kDirRY; ++r) acc[r] = 0.f;
 #pragma unroll
             for (int kz = 0; kz < 3; ++kz) {
                 if (kz < c.KD) {
+                    const float *gpl = gs + kz * plane;
 #pragma unroll
-                    for (int ky = 0; ky < 3; ++ky) {
-                        const int oy = iy + 1 - ky;
+                    for (int ry = 0; ry < kDirRY + 2; ++ry) {
+                        // g row oy = y0 + ry - 1 reaches input row iy = oy - 1 + ky, i.e. r = ry - 2 + ky
+                        const int oy = y0 + ry - 1;
                         if (oy >= 0 && oy < c.OH) {
-                            const float *row = gs + kz * plane + oy * c.OW;
-                            const float *wr = ws + ci * 27 + kz * 9 + ky * 3;
-                            const float w0 = wr[0], w1 = wr[1], w2 = wr[2];
-                            // r[m] = g at ox = x0 - 1 + m; ix = x0 + j takes ox = ix + 1 - kx = x0 + j + 1 - kx
-                            float r[kDirXS + 2];
+                            const float *row = gpl + oy * c.OW;
+                            float u[3];  // u[m] = g at ox = px - 1 + m, which px takes with kx = 2 - m
 #pragma unroll
-                            for (int m = 0; m < kDirXS + 2; ++m) {
-                                const int ox = x0 - 1 + m;
-                                r[m] = (ox >= 0 && ox < c.OW) ? row[ox] : 0.f;
+                            for (int m = 0; m < 3; ++m) {
+                                const int ox = px - 1 + m;
+                                u[m] = (ox >= 0 && ox < c.OW) ? row[ox] : 0.f;
                             }
 #pragma unroll
-                            for (int j = 0; j < kDirXS; ++j)
-                                acc[j] = fmaf(w2, r[j], fmaf(w1, r[j + 1], fmaf(w0, r[j + 2], acc[j])));
+                            for (int ky = 0; ky < 3; ++ky) {
+                                const int r = ry - 2 + ky;
+                                if (r >= 0 && r < kDirRY) {
+                                    const float *wk = w + kz * 9 + ky * 3;
+                                    acc[r] = fmaf(wk[0], u[2], fmaf(wk[1], u[1], fmaf(wk[2], u[0], acc[r])));
+                                }
+                            }
                         }
                     }
                 }
             }
-            float *o = gin + (((size_t)n * c.CI + ci) * c.OD + iz) * plane + (size_t)iy * c.OW;
+            if (px < c.OW) {
 #pragma unroll
-            for (int j = 0; j < kDirXS; ++j)
-                if (x0 + j < c.OW) o[x0 + j] = acc[j];
+                for (int r = 0; r < kDirRY; ++r)
+                    if (y0 + r < c.OH) o[(size_t)(y0 + r) * c.OW + px] = acc[r];
+            }
         }
     }
 }
@@ -983,9 +1035,11 @@ int log2_exact(int v) {
 }
 
 // The one-output-channel layers that the CUDA-core kernels take (see k_wgrad_co1): stride 1,
-// "same" padding, 3 x 3 in-plane taps, at most two work items of kDirXS positions per thread in
-// the forward kernel, shared memory within the opt-in limit.
+// "same" padding, 3 x 3 in-plane taps, at most two warp tasks per warp in the forward kernel, a
+// channel's stored planes within the forward kernel's register prefetch, shared memory within the
+// opt-in limit.
 constexpr size_t kDirSmemMax = 200 * 1024;
+constexpr int kDirPlanesPerBlock = 4;  // weight gradient: (n, z) planes per block and partial
 
 gm::nn::DirectConv direct_view(const Layer &l, int N) {
     gm::nn::DirectConv c{};
@@ -1002,6 +1056,7 @@ gm::nn::DirectConv direct_view(const Layer &l, int N) {
     c.us1 = l.up[1] == 2 ? 1 : 0;
     c.us2 = l.up[2] == 2 ? 1 : 0;
     c.relu = l.relu ? 1 : 0;
+    c.planes_per_block = kDirPlanesPerBlock;
     return c;
 }
 
@@ -1010,8 +1065,9 @@ bool direct_ok(const Layer &l) {
     if (d.CO != 1 || d.SD != 1 || d.SH != 1 || d.SW != 1 || d.KH != 3 || d.KW != 3 || d.PH != 1 || d.PW != 1)
         return false;
     if ((d.KD != 1 && d.KD != 3) || d.PD != d.KD / 2 || d.OD != d.ID || d.OH != d.IH || d.OW != d.IW) return false;
-    if ((long long)d.OH * ((d.OW + gm::nn::kDirXS - 1) / gm::nn::kDirXS) > 2LL * gm::nn::kDirThreads) return false;
     const gm::nn::DirectConv c = direct_view(l, 1);
+    if (gm::nn::dir_tasks(c) > gm::nn::kDirTasksMax) return false;
+    if ((long long)c.KD * c.LH * c.LW > (long long)gm::nn::kDirPre * gm::nn::kDirThreads) return false;
     for (int mode = 0; mode < 3; ++mode)
         if (sizeof(float) * gm::nn::direct_smem_floats(mode, c) > kDirSmemMax) return false;
     return true;
@@ -1120,17 +1176,20 @@ int launch_tc(const Layer &l, int N, const __nv_bfloat16 *wpk, const float *bias
 // Weight-gradient partials of layer l for a batch of N: one per (n, output plane) on the CUDA-core
 // path, one per position chunk on the tensor cores.
 int wgrad_chunks(const Layer &l, int N) {
-    if (direct_ok(l)) return N * l.d.OD;
+    if (direct_ok(l)) return (N * l.d.OD + kDirPlanesPerBlock - 1) / kDirPlanesPerBlock;
     const long long Q = (long long)N * l.d.OD * l.d.OH * l.d.OW;
     return (int)((Q + wgrad_chunk(l, N) - 1) / wgrad_chunk(l, N));
 }
 
 // One convolution of layer l in mode MODE: the CUDA-core kernels for a one-output-channel layer,
 // else the tensor-core GEMM (launch_tc, same arguments); returns the launches made.
+// The forward and data-gradient kernels give one block per plane: with fewer planes than two
+// per SM (small batches) the tensor-core kernels, which tile positions, keep the GPU busier.
 template <int MODE>
 int launch_conv(const Layer &l, int N, const __nv_bfloat16 *wpk, const float *bias, const float *act,
                 const float *grad, float *out, float *out2, int *err, cudaStream_t s) {
-    if (!direct_ok(l)) return launch_tc<MODE>(l, N, wpk, bias, act, grad, out, out2, err, s);
+    const bool few_planes = MODE != gm::nn::WGRAD && (long long)N * l.d.OD < 2LL * 152;
+    if (!direct_ok(l) || few_planes) return launch_tc<MODE>(l, N, wpk, bias, act, grad, out, out2, err, s);
     const gm::nn::DirectConv c = direct_view(l, N);
     const size_t smem = sizeof(float) * gm::nn::direct_smem_floats(MODE, c);
     const int planes = N * l.d.OD;
@@ -1139,7 +1198,8 @@ int launch_conv(const Layer &l, int N, const __nv_bfloat16 *wpk, const float *bi
     else if (MODE == gm::nn::DGRAD)
         gm::nn::k_dgrad_co1<<<planes, gm::nn::kDirThreads, smem, s>>>(grad, wpk, l.kd, c, out);
     else
-        gm::nn::k_wgrad_co1<<<dim3(planes, l.d.CI), gm::nn::kDirThreads, smem, s>>>(act, grad, c, out, out2);
+        gm::nn::k_wgrad_co1<<<dim3(wgrad_chunks(l, N), l.d.CI), gm::nn::kDirThreads, smem, s>>>(act, grad, c, out,
+                                                                                                  out2);
     return 1;
 }
 

@@ -5,8 +5,9 @@ The kernels carry each FP32 activation and gradient as two BF16 terms (hi + lo: 
 representation error about 1.3e-6) and accumulate the products in FP32 over K = 9 or 27 taps x
 up to 512 channels (or over all positions for the weight gradient, whose lo x lo term is left
 out, about 1.3e-6 of each product): a relative 2-norm error of order 2e-6; the bound is 1e-5.  The geometries
-cover one input channel, one output channel, odd sizes that leave ragged 128-row tiles,
-stride 2, 3-D kernels and two 256-column tiles.
+cover one input channel, one output channel (on the tensor cores for few (sample, plane) pairs,
+on the CUDA-core kernels for many), odd sizes that leave ragged 128-row tiles, stride 2, 3-D
+kernels and two 256-column tiles.
 """
 import numpy as np
 import pytest
@@ -26,6 +27,9 @@ GEOMS = [
     (2, 16, 1, 5, 9, 7, 3, 1),
     (1, 64, 32, 4, 5, 3, 3, 1),
     (2, 8, 16, 3, 33, 31, 3, 2),
+    # one output channel with enough (sample, plane) pairs that every mode takes the CUDA-core kernels
+    (20, 16, 1, 16, 12, 21, 3, 1),
+    (24, 4, 1, 13, 7, 33, 1, 1),
 ]
 
 
