@@ -16,7 +16,7 @@ namespace gm {
 namespace {
 
 constexpr int kPairs = 8;   // two-row transforms per row-kernel CTA (many rows)
-constexpr int kLstep = 2;   // layers per step in the column kernels
+constexpr int kLstep = kColLayerStep;
 
 // Row kernels with few CTAs' worth of rows use one-warp CTAs of a single two-row transform.
 inline bool few_rows(int rows, int nlayers) {

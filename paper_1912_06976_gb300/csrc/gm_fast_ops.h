@@ -26,6 +26,8 @@ struct gm_plan;
 
 namespace gm {
 
+constexpr int kColLayerStep = 2;  // layers per step in the column kernels
+
 template <typename R> struct XOps {
     cudaError_t (*r2c)(const io_t<R> *in, int rows, int row_len, int nlayers, cpx_t<R> *out, int out_rows, const void *tw,
                        cudaStream_t s);
