@@ -284,22 +284,36 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
                 }
             }
             const int nrow = p.taps << p.lg;
+            // Rows run through the channels of one tap before the next tap, and a position's
+            // bounds and spatial offset depend on the tap only: they are recomputed when the
+            // row's tap changes (for 8 or more channels, once per 8-row group at most and the same
+            // in every lane of the warp).  off[e] < 0: the tapped input lies outside the volume.
+            int ctap = -1, off[2] = {-1, -1};
+            const float *sbase[2] = {act, act};
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                if (pn[e] >= 0) sbase[e] = act + (size_t)pn[e] * d.CI * lsz;
             for (int grp = 0; grp < 16; ++grp) {  // A rows (tap, ci), then the ones row
                 const int row = grp * 8 + rr, kk = m0 + row;
                 float v[2] = {0.f, 0.f};
                 if (kk < nrow) {
                     const int tap = kk >> p.lg, ci = kk & cmask;
-                    int kz, ky, kx;
-                    decode_tap(tap, kz, ky, kx);
+                    if (tap != ctap) {
+                        ctap = tap;
+                        int kz, ky, kx;
+                        decode_tap(tap, kz, ky, kx);
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        if (pn[e] < 0) continue;
-                        const int a = pz[e] * d.SD + kz - d.PD, b = py[e] * d.SH + ky - d.PH,
-                                  c = px[e] * d.SW + kx - d.PW;
-                        if (a >= 0 && a < d.ID && b >= 0 && b < d.IH && c >= 0 && c < d.IW)
-                            v[e] = act[((size_t)pn[e] * d.CI + ci) * lsz +
-                                       ((size_t)(a >> p.us[0]) * p.LH + (b >> p.us[1])) * p.LW + (c >> p.us[2])];
+                        for (int e = 0; e < 2; ++e) {
+                            const int a = pz[e] * d.SD + kz - d.PD, b = py[e] * d.SH + ky - d.PH,
+                                      c = px[e] * d.SW + kx - d.PW;
+                            off[e] = (pn[e] >= 0 && a >= 0 && a < d.ID && b >= 0 && b < d.IH && c >= 0 && c < d.IW)
+                                         ? ((a >> p.us[0]) * p.LH + (b >> p.us[1])) * p.LW + (c >> p.us[2])
+                                         : -1;
+                        }
                     }
+#pragma unroll
+                    for (int e = 0; e < 2; ++e)
+                        if (off[e] >= 0) v[e] = sbase[e][(size_t)ci * lsz + off[e]];
                 } else if (kk == nrow) {
                     v[0] = pn[0] >= 0 ? 1.f : 0.f;
                     v[1] = pn[1] >= 0 ? 1.f : 0.f;
