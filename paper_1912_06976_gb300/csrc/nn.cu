@@ -172,6 +172,21 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
     const uint32_t idesc = gm::tc::instr_desc_bf16(128, bn);
     bool ok = true;
     int committed = -1;  // last K block whose MMAs were committed (the same in every thread)
+    // WGRAD: the two positions this lane gathers in the current K block (q = linear position;
+    // sample, z, y, x), decoded once here and carried from block to block
+    int wq[2] = {0, 0}, wn[2] = {0, 0}, wz[2] = {0, 0}, wy[2] = {0, 0}, wx[2] = {0, 0};
+    if (MODE == WGRAD) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int q = q0 + (t >> 5) * 8 + 2 * ((t & 31) >> 3) + e;
+            wq[e] = q;
+            wn[e] = q / osz;
+            const int o = q - wn[e] * osz;
+            wx[e] = o % d.OW;
+            wy[e] = (o / d.OW) % d.OH;
+            wz[e] = o / (d.OW * d.OH);
+        }
+    }
 
     for (int it = 0; it < nkb; ++it) {
         const int kb = kb0 + it;
@@ -272,16 +287,12 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
             int pn[2], pz[2], py[2], px[2], po[2];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-                const int q = q0 + kb * kTcBK + warp * 8 + 2 * j + e;
-                pn[e] = -1;
-                pz[e] = py[e] = px[e] = po[e] = 0;
-                if (q < p.kreal) {
-                    pn[e] = q / osz;
-                    po[e] = q - pn[e] * osz;
-                    px[e] = po[e] % d.OW;
-                    py[e] = (po[e] / d.OW) % d.OH;
-                    pz[e] = po[e] / (d.OW * d.OH);
-                }
+                const bool in = wq[e] < p.kreal;
+                pn[e] = in ? wn[e] : -1;
+                pz[e] = wz[e];
+                py[e] = wy[e];
+                px[e] = wx[e];
+                po[e] = in ? (wz[e] * d.OH + wy[e]) * d.OW + wx[e] : 0;
             }
             const int nrow = p.taps << p.lg;
             // Rows run through the channels of one tap before the next tap, and a position's
@@ -293,8 +304,10 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
 #pragma unroll
             for (int e = 0; e < 2; ++e)
                 if (pn[e] >= 0) sbase[e] = act + (size_t)pn[e] * d.CI * lsz;
-            for (int grp = 0; grp < 16; ++grp) {  // A rows (tap, ci), then the ones row
-                const int row = grp * 8 + rr, kk = m0 + row;
+            // row grp * 8 + rr of the tile: shared-memory offset tile_offset(row, warp) + 4 j
+            uint32_t so = gm::tc::tile_offset(rr, warp) + 4 * j;
+            int kk = m0 + rr;
+            for (int grp = 0; grp < 16; ++grp, kk += 8, so += 1024) {  // A rows (tap, ci), then the ones row
                 float v[2] = {0.f, 0.f};
                 if (kk < nrow) {
                     const int tap = kk >> p.lg, ci = kk & cmask;
@@ -320,8 +333,8 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
                 }
                 uint32_t h, lo;
                 split_bf16x2(v[0], v[1], &h, &lo);
-                *reinterpret_cast<uint32_t *>(sa + gm::tc::tile_offset(row, warp) + 4 * j) = h;
-                *reinterpret_cast<uint32_t *>(sal + gm::tc::tile_offset(row, warp) + 4 * j) = lo;
+                *reinterpret_cast<uint32_t *>(sa + so) = h;
+                *reinterpret_cast<uint32_t *>(sal + so) = lo;
             }
             for (int grp = 0; grp < (bn >> 3); ++grp) {  // B rows co
                 const int row = grp * 8 + rr, col = n0 + row;
@@ -335,6 +348,22 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
                 split_bf16x2(v[0], v[1], &h, &lo);
                 *reinterpret_cast<uint32_t *>(sb + gm::tc::tile_offset(row, warp) + 4 * j) = h;
                 *reinterpret_cast<uint32_t *>(sbl + gm::tc::tile_offset(row, warp) + 4 * j) = lo;
+            }
+            // the next K block's positions: kTcBK further along (x fastest, then y, z, sample)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                wq[e] += kTcBK;
+                wx[e] += kTcBK;
+                while (wx[e] >= d.OW) {
+                    wx[e] -= d.OW;
+                    if (++wy[e] == d.OH) {
+                        wy[e] = 0;
+                        if (++wz[e] == d.OD) {
+                            wz[e] = 0;
+                            ++wn[e];
+                        }
+                    }
+                }
             }
         }
         // ---- B of FWD / DGRAD: bn rows x 8 core columns of packed weights
