@@ -124,7 +124,7 @@ __device__ __forceinline__ void decode_tap(int tap, int &kz, int &ky, int &kx) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict__ act, const float *__restrict__ grad,
+__global__ void __launch_bounds__(kTcThreads, 3) k_conv_tc(const float *__restrict__ act, const float *__restrict__ grad,
                                                         const __nv_bfloat16 *__restrict__ wpk,
                                                         const float *__restrict__ bias, float *__restrict__ out,
                                                         float *__restrict__ out2, ConvGemm p, int bn,
@@ -172,20 +172,16 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
     const uint32_t idesc = gm::tc::instr_desc_bf16(128, bn);
     bool ok = true;
     int committed = -1;  // last K block whose MMAs were committed (the same in every thread)
-    // WGRAD: the two positions this lane gathers in the current K block (q = linear position;
-    // sample, z, y, x), decoded once here and carried from block to block
-    int wq[2] = {0, 0}, wn[2] = {0, 0}, wz[2] = {0, 0}, wy[2] = {0, 0}, wx[2] = {0, 0};
+    // WGRAD: the first of the 8 positions this thread's warp gathers in the current K block
+    // (q = linear position; sample, z, y, x), decoded once here and carried from block to block
+    int wq = 0, wn = 0, wz = 0, wy = 0, wx = 0;
     if (MODE == WGRAD) {
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int q = q0 + (t >> 5) * 8 + 2 * ((t & 31) >> 3) + e;
-            wq[e] = q;
-            wn[e] = q / osz;
-            const int o = q - wn[e] * osz;
-            wx[e] = o % d.OW;
-            wy[e] = (o / d.OW) % d.OH;
-            wz[e] = o / (d.OW * d.OH);
-        }
+        wq = q0 + (t >> 5) * 8;
+        wn = wq / osz;
+        const int o = wq - wn * osz;
+        wx = o % d.OW;
+        wy = (o / d.OW) % d.OH;
+        wz = o / (d.OW * d.OH);
     }
 
     for (int it = 0; it < nkb; ++it) {
@@ -280,35 +276,47 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
                 *reinterpret_cast<uint4 *>(sal + gm::tc::tile_offset(r, kc)) = pl;
             }
         } else {
-            // WGRAD: warp w fills core column w (positions 8w..8w+7 of the block) of A and B;
-            // lane (row r = lane & 7, pair j = lane >> 3) holds positions 8w + 2j and 8w + 2j + 1,
-            // so one 4-byte store per lane fills one 8 x 8 core matrix
-            const int warp = t >> 5, lane = t & 31, rr = lane & 7, j = lane >> 3;
-            int pn[2], pz[2], py[2], px[2], po[2];
+            // WGRAD: warp w fills core column w (positions 8w..8w+7 of the block) of A and B, a lane
+            // whole 16-byte core-matrix rows (the row's 8 positions): A rows 4 lane .. 4 lane + 3
+            // (consecutive channels of one tap when CI >= 4, so a position's bounds and offset,
+            // which depend on the tap only, are computed once per tap), B rows lane, lane + 32, ...
+            // Each lane stores its four A rows in a rotated order so that the 32 stores of one
+            // instruction cover all eight row slots of the core matrices (four-way, not 16-way,
+            // bank conflicts).
+            const int warp = t >> 5, lane = t & 31;
+            // the 8 positions: sample (-1 past the end), (z, y, x), offset in the sample's volume
+            int smp[8], pz8[8], py8[8], px8[8], po8[8];
+            {
+                int q = wq, n = wn, z = wz, y = wy, x = wx;
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const bool in = wq[e] < p.kreal;
-                pn[e] = in ? wn[e] : -1;
-                pz[e] = wz[e];
-                py[e] = wy[e];
-                px[e] = wx[e];
-                po[e] = in ? (wz[e] * d.OH + wy[e]) * d.OW + wx[e] : 0;
+                for (int e = 0; e < 8; ++e) {
+                    smp[e] = q < p.kreal ? n : -1;
+                    pz8[e] = z;
+                    py8[e] = y;
+                    px8[e] = x;
+                    po8[e] = (z * d.OH + y) * d.OW + x;
+                    ++q;
+                    if (++x == d.OW) {
+                        x = 0;
+                        if (++y == d.OH) {
+                            y = 0;
+                            if (++z == d.OD) {
+                                z = 0;
+                                ++n;
+                            }
+                        }
+                    }
+                }
             }
             const int nrow = p.taps << p.lg;
-            // Rows run through the channels of one tap before the next tap, and a position's
-            // bounds and spatial offset depend on the tap only: they are recomputed when the
-            // row's tap changes (for 8 or more channels, once per 8-row group at most and the same
-            // in every lane of the warp).  off[e] < 0: the tapped input lies outside the volume.
-            int ctap = -1, off[2] = {-1, -1};
-            const float *sbase[2] = {act, act};
+            const int rot = (lane >> 1) & 3;
+            int ctap = -1, off[8];
 #pragma unroll
-            for (int e = 0; e < 2; ++e)
-                if (pn[e] >= 0) sbase[e] = act + (size_t)pn[e] * d.CI * lsz;
-            // row grp * 8 + rr of the tile: shared-memory offset tile_offset(row, warp) + 4 j
-            uint32_t so = gm::tc::tile_offset(rr, warp) + 4 * j;
-            int kk = m0 + rr;
-            for (int grp = 0; grp < 16; ++grp, kk += 8, so += 1024) {  // A rows (tap, ci), then the ones row
-                float v[2] = {0.f, 0.f};
+            for (int e = 0; e < 8; ++e) off[e] = -1;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int row = 4 * lane + ((r + rot) & 3), kk = m0 + row;
+                float v[8];
                 if (kk < nrow) {
                     const int tap = kk >> p.lg, ci = kk & cmask;
                     if (tap != ctap) {
@@ -316,52 +324,56 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const float *__restrict_
                         int kz, ky, kx;
                         decode_tap(tap, kz, ky, kx);
 #pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const int a = pz[e] * d.SD + kz - d.PD, b = py[e] * d.SH + ky - d.PH,
-                                      c = px[e] * d.SW + kx - d.PW;
-                            off[e] = (pn[e] >= 0 && a >= 0 && a < d.ID && b >= 0 && b < d.IH && c >= 0 && c < d.IW)
-                                         ? ((a >> p.us[0]) * p.LH + (b >> p.us[1])) * p.LW + (c >> p.us[2])
+                        for (int e = 0; e < 8; ++e) {
+                            const int aa = pz8[e] * d.SD + kz - d.PD, bb = py8[e] * d.SH + ky - d.PH,
+                                      cc = px8[e] * d.SW + kx - d.PW;
+                            off[e] = (smp[e] >= 0 && aa >= 0 && aa < d.ID && bb >= 0 && bb < d.IH && cc >= 0 &&
+                                      cc < d.IW)
+                                         ? smp[e] * d.CI * (int)lsz +
+                                               ((aa >> p.us[0]) * p.LH + (bb >> p.us[1])) * p.LW + (cc >> p.us[2])
                                          : -1;
                         }
                     }
+                    const int cofs = ci * (int)lsz;
 #pragma unroll
-                    for (int e = 0; e < 2; ++e)
-                        if (off[e] >= 0) v[e] = sbase[e][(size_t)ci * lsz + off[e]];
-                } else if (kk == nrow) {
-                    v[0] = pn[0] >= 0 ? 1.f : 0.f;
-                    v[1] = pn[1] >= 0 ? 1.f : 0.f;
+                    for (int e = 0; e < 8; ++e) v[e] = off[e] >= 0 ? act[off[e] + cofs] : 0.f;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) v[e] = (kk == nrow && smp[e] >= 0) ? 1.f : 0.f;  // the ones row
                 }
-                uint32_t h, lo;
-                split_bf16x2(v[0], v[1], &h, &lo);
-                *reinterpret_cast<uint32_t *>(sa + so) = h;
-                *reinterpret_cast<uint32_t *>(sal + so) = lo;
+                uint4 h, lo;
+                split_bf16x2(v[0], v[1], &h.x, &lo.x);
+                split_bf16x2(v[2], v[3], &h.y, &lo.y);
+                split_bf16x2(v[4], v[5], &h.z, &lo.z);
+                split_bf16x2(v[6], v[7], &h.w, &lo.w);
+                *reinterpret_cast<uint4 *>(sa + gm::tc::tile_offset(row, warp)) = h;
+                *reinterpret_cast<uint4 *>(sal + gm::tc::tile_offset(row, warp)) = lo;
             }
-            for (int grp = 0; grp < (bn >> 3); ++grp) {  // B rows co
-                const int row = grp * 8 + rr, col = n0 + row;
-                float v[2] = {0.f, 0.f};
-                if (col < p.ncols) {
+            for (int row = lane; row < bn; row += 32) {  // B rows co
+                const int col = n0 + row;
+                float v[8];
 #pragma unroll
-                    for (int e = 0; e < 2; ++e)
-                        if (pn[e] >= 0) v[e] = grad[((size_t)pn[e] * d.CO + col) * osz + po[e]];
-                }
-                uint32_t h, lo;
-                split_bf16x2(v[0], v[1], &h, &lo);
-                *reinterpret_cast<uint32_t *>(sb + gm::tc::tile_offset(row, warp) + 4 * j) = h;
-                *reinterpret_cast<uint32_t *>(sbl + gm::tc::tile_offset(row, warp) + 4 * j) = lo;
+                for (int e = 0; e < 8; ++e)
+                    v[e] = (col < p.ncols && smp[e] >= 0) ? grad[((size_t)smp[e] * d.CO + col) * osz + po8[e]] : 0.f;
+                uint4 h, lo;
+                split_bf16x2(v[0], v[1], &h.x, &lo.x);
+                split_bf16x2(v[2], v[3], &h.y, &lo.y);
+                split_bf16x2(v[4], v[5], &h.z, &lo.z);
+                split_bf16x2(v[6], v[7], &h.w, &lo.w);
+                *reinterpret_cast<uint4 *>(sb + gm::tc::tile_offset(row, warp)) = h;
+                *reinterpret_cast<uint4 *>(sbl + gm::tc::tile_offset(row, warp)) = lo;
             }
-            // the next K block's positions: kTcBK further along (x fastest, then y, z, sample)
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                wq[e] += kTcBK;
-                wx[e] += kTcBK;
-                while (wx[e] >= d.OW) {
-                    wx[e] -= d.OW;
-                    if (++wy[e] == d.OH) {
-                        wy[e] = 0;
-                        if (++wz[e] == d.OD) {
-                            wz[e] = 0;
-                            ++wn[e];
-                        }
+            // the next K block's first position of this warp: kTcBK further along (x fastest, then
+            // y, z, sample)
+            wq += kTcBK;
+            wx += kTcBK;
+            while (wx >= d.OW) {
+                wx -= d.OW;
+                if (++wy == d.OH) {
+                    wy = 0;
+                    if (++wz == d.OD) {
+                        wz = 0;
+                        ++wn;
                     }
                 }
             }
