@@ -314,6 +314,55 @@ def oracle_dense_timings(names=("grav16", "mag64"), budget_s: float = 2.0):
 
 
 # ----------------------------------------------------------------------------- reference arm
+def roofline_of(ktimes, inf, step_ms, peak, peak_kind, profiled_traffic_for=None):
+    """Roofline record of the dominant kernel (the one with the most device time in `ktimes`,
+    {name: (launches, total ms)}): algorithmic bytes per launch over its mean launch time against
+    the measured copy rate `peak` (GB/s), and, for the column kernels, 5 N log2 N flops per complex
+    transform of length N plus the depth multiply-accumulate against the FP32 peak.  The bound
+    reported is the roof that the kernel's arithmetic intensity selects (above the ridge point of
+    the two peaks: the ALU roof)."""
+    import math
+
+    w_el = 4
+    spec_bytes = inf.spectrum_bytes  # as stored: complex, or real even (a quarter) for gravity
+    alg = {"fwd_rows_r2c": w_el * inf.n_model, "fwd_cols_mac": spec_bytes, "fwd_cols_inv": 0,
+           "fwd_rows_c2r": w_el * inf.n_data, "tr_rows_r2c": w_el * inf.n_data, "tr_cols": spec_bytes,
+           "tr_rows_c2r": w_el * inf.n_model}
+    dom = max(ktimes, key=lambda k: ktimes[k][1])
+    dom_ms = ktimes[dom][1] / ktimes[dom][0]
+    achieved = alg[dom] / (dom_ms / 1e3) / 1e9
+    traffic = profiled_traffic(dom, profiled_traffic_for) if profiled_traffic_for else None
+    apply_bytes = w_el * (inf.n_model + inf.n_data) + spec_bytes  # per forward or transpose product
+    fx, fy, kx, nz = inf.fft_nx, inf.fft_ny, inf.spec_nx, inf.nz
+    tf_y = 5.0 * fy * math.log2(fy)
+    mac = (4.0 if inf.spectrum_real else 8.0) * kx * nz * fy
+    col_flops = {"fwd_cols_mac": kx * nz * tf_y + mac + kx * tf_y, "tr_cols": kx * tf_y + mac + kx * nz * tf_y}
+    hbm = {"kernel": dom, "achieved_gbs": achieved, "peak_gbs": peak, "frac": achieved / peak,
+           "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)", "algorithmic_bytes_per_launch": alg[dom]}
+    if dom in col_flops:
+        alu = {"kernel": dom, "gflop_per_launch": col_flops[dom] / 1e9,
+               "achieved_tflops": col_flops[dom] / (dom_ms / 1e3) / 1e12, "peak_tflops": FP32_PEAK_TFLOPS,
+               "frac": col_flops[dom] / (dom_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+               "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+    else:
+        alu = None
+    # With the real even spectrum the column kernels do ~25 flop per algorithmic byte, above the
+    # ridge (~12 flop/B), so the FP32 ALU roof is the lower one.
+    ridge = FP32_PEAK_TFLOPS * 1e12 / (peak * 1e9)
+    intensity = (col_flops[dom] / alg[dom]) if (dom in col_flops and alg[dom]) else 0.0
+    common = {"kernel": dom, "traffic": traffic, "algorithmic_bytes_per_launch": alg[dom],
+              "spectrum_form": "real even (quarter)" if inf.spectrum_real else "complex",
+              "kernel_ms_per_launch": dom_ms, "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
+              "apply_effective_gbs": 2 * apply_bytes / (step_ms / 1e3) / 1e9,
+              "apply_frac_of_hbm": 2 * apply_bytes / (step_ms / 1e3) / 1e9 / peak,
+              "kernel_share": {k: v[1] / sum(x[1] for x in ktimes.values()) for k, v in ktimes.items()}}
+    if alu is not None and intensity > ridge:
+        return {"bound": "alu", "achieved": alu["achieved_tflops"], "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": alu["frac"], "peak_source": alu["peak_source"], **common, "hbm_view": hbm}
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": hbm["peak_source"], **common, "alu_view": alu}
+
+
 def gpu_name():
     try:
         import torch
@@ -495,53 +544,7 @@ def run_ours(args):
     gpu_launches = sum(v[0] for v in ktimes.values())
     ms_per_step_with_kernel_events = (sum(per_step_timed) / args.steps) if per_step_timed else None
 
-    # roofline of the dominant kernel: algorithmic bytes per launch / its mean launch time
-    w_el = 4
-    spec_bytes = inf.spectrum_bytes  # as stored: complex, or real even (a quarter) for gravity
-    alg = {"fwd_rows_r2c": w_el * inf.n_model, "fwd_cols_mac": spec_bytes, "fwd_cols_inv": 0,
-           "fwd_rows_c2r": w_el * inf.n_data, "tr_rows_r2c": w_el * inf.n_data, "tr_cols": spec_bytes,
-           "tr_rows_c2r": w_el * inf.n_model}
-    dom = max(ktimes, key=lambda k: ktimes[k][1])
-    dom_ms = ktimes[dom][1] / ktimes[dom][0]
-    peak, peak_kind = measured_peaks()
-    achieved = alg[dom] / (dom_ms / 1e3) / 1e9
-    traffic = profiled_traffic(dom, w.name)
-    apply_bytes = w_el * (inf.n_model + inf.n_data) + spec_bytes  # per forward or transpose product
-    step_ms = t_ms / args.steps
-    # ALU view of the same kernel: 5 N log2 N flops per complex transform of length N (the usual
-    # count), 4 flops per real x complex (8 per complex x complex) depth multiply-accumulate
-    import math
-
-    fx, fy, kx, nz = inf.fft_nx, inf.fft_ny, inf.spec_nx, inf.nz
-    tf_y = 5.0 * fy * math.log2(fy)
-    mac = (4.0 if inf.spectrum_real else 8.0) * kx * nz * fy
-    col_flops = {"fwd_cols_mac": kx * nz * tf_y + mac + kx * tf_y, "tr_cols": kx * tf_y + mac + kx * nz * tf_y}
-    hbm = {"kernel": dom, "achieved_gbs": achieved, "peak_gbs": peak, "frac": achieved / peak,
-           "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)", "algorithmic_bytes_per_launch": alg[dom]}
-    if dom in col_flops:
-        alu = {"kernel": dom, "gflop_per_launch": col_flops[dom] / 1e9,
-               "achieved_tflops": col_flops[dom] / (dom_ms / 1e3) / 1e12, "peak_tflops": FP32_PEAK_TFLOPS,
-               "frac": col_flops[dom] / (dom_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
-               "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
-    else:
-        alu = None
-    # The roof that bounds the kernel: its arithmetic intensity against the ridge point of the two
-    # peaks.  With the real even spectrum the column kernels do ~25 flop per algorithmic byte, above
-    # the ridge (~12 flop/B), so the FP32 ALU roof is the lower one.
-    ridge = FP32_PEAK_TFLOPS * 1e12 / (peak * 1e9)
-    intensity = (col_flops[dom] / alg[dom]) if (dom in col_flops and alg[dom]) else 0.0
-    common = {"kernel": dom, "traffic": traffic, "algorithmic_bytes_per_launch": alg[dom],
-              "spectrum_form": "real even (quarter)" if inf.spectrum_real else "complex",
-              "kernel_ms_per_launch": dom_ms, "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
-              "apply_effective_gbs": 2 * apply_bytes / (step_ms / 1e3) / 1e9,
-              "apply_frac_of_hbm": 2 * apply_bytes / (step_ms / 1e3) / 1e9 / peak,
-              "kernel_share": {k: v[1] / sum(x[1] for x in ktimes.values()) for k, v in ktimes.items()}}
-    if alu is not None and intensity > ridge:
-        roofline = {"bound": "alu", "achieved": alu["achieved_tflops"], "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": alu["frac"], "peak_source": alu["peak_source"], **common, "hbm_view": hbm}
-    else:
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "peak_source": hbm["peak_source"], **common, "alu_view": alu}
+    roofline = roofline_of(ktimes, inf, t_ms / args.steps, *measured_peaks(), profiled_traffic_for=w.name)
 
     # end to end through the host-buffer entry points (pinned host memory, copies timed).  Every
     # step copies its model in and its data out (forward, stream 1) and its data in and its model
