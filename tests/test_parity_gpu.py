@@ -578,3 +578,27 @@ def test_host_buffer_forward_and_transpose_from_two_threads(gm):
     for b in om:
         assert torch.equal(b, ref_m)
     op.close()
+
+
+@pytest.mark.parametrize("name", ["mag64", "grav16"])
+def test_layer_grouping_override_keeps_the_products(gm, monkeypatch, name):
+    """The column kernels' layers per CTA group (a tuning choice) changes only the order of the
+    depth sum: ragged last groups and one layer per group give the default products to FP32
+    rounding."""
+    import torch
+
+    w = W.WORKLOADS[name]
+    m = torch.as_tensor(W.model(name, 0), dtype=torch.float32).cuda()
+    d = torch.as_tensor(W.data(name, 0), dtype=torch.float32).cuda()
+    monkeypatch.delenv("GM_FWD_LAYERS_PER_GROUP", raising=False)
+    monkeypatch.delenv("GM_TR_LAYERS_PER_GROUP", raising=False)
+    op = gm.Operator.from_workload(w, precision=gm.F32)
+    ref_d, ref_m = op.forward(m).cpu(), op.transpose(d).cpu()
+    op.close()
+    for fwd, tr in ((1, 1), (3, 2), (5, 7), (w.nz, w.nz)):
+        monkeypatch.setenv("GM_FWD_LAYERS_PER_GROUP", str(fwd))
+        monkeypatch.setenv("GM_TR_LAYERS_PER_GROUP", str(tr))
+        op = gm.Operator.from_workload(w, precision=gm.F32)
+        assert_close(op.forward(m).cpu().numpy(), ref_d.numpy(), 1e-6, f"forward {fwd}")
+        assert_close(op.transpose(d).cpu().numpy(), ref_m.numpy(), 1e-6, f"transpose {tr}")
+        op.close()
