@@ -32,7 +32,9 @@ def _declared_functions(header=None):
 def test_header_declares_the_boundary():
     names = _declared_functions("gravmag.h")
     for required in ("grav_mag_setup", "grav_mag_setup_ex", "apply_forward", "apply_transpose",
-                     "grav_mag_destroy", "gm_status_string", "gm_cgls"):
+                     "apply_forward_host", "apply_transpose_host", "apply_forward_host_async",
+                     "apply_transpose_host_async", "grav_mag_destroy", "gm_status_string", "gm_cgls",
+                     "gm_cgls_noalloc"):
         assert required in names
     net = _declared_functions("gm_warmstart.h")
     for required in ("gm_net_create", "gm_net_forward", "gm_net_train_step", "gm_net_get_params"):
@@ -107,6 +109,23 @@ def test_setup_without_a_device_fails_cleanly(lib):
     assert so.gm_last_status() == lib.GM_ENODEV
     assert so.apply_forward(None, None, None, None) == lib.GM_EINVAL
     assert so.grav_mag_destroy(None) == lib.GM_OK
+
+
+def test_operator_entry_points_reject_a_null_handle_before_touching_a_device(lib):
+    """Every call on a handle checks it first: a NULL handle is GM_EINVAL with a message, on any
+    machine, with or without a GPU."""
+    import ctypes
+
+    so = lib.load()
+    buf = (ctypes.c_float * 16)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    for fn in ("apply_forward", "apply_transpose", "apply_forward_host", "apply_transpose_host",
+               "apply_forward_host_async", "apply_transpose_host_async"):
+        assert getattr(so, fn)(None, p, p, None) == lib.GM_EINVAL, fn
+        assert so.gm_last_status() == lib.GM_EINVAL
+        assert so.gm_last_error()
+    assert so.gm_cgls(None, p, None, p, 0.1, 3, None, None) == lib.GM_EINVAL
+    assert so.gm_cgls_noalloc(None, p, None, p, 0.1, 3, None, None) == lib.GM_EINVAL
 
 
 def test_network_rejects_bad_arguments_without_a_device(lib):
